@@ -1,0 +1,438 @@
+"""Benchmark of the GB300 relativistic lattice Boltzmann path.
+
+Metric: MLUPS (million lattice-cell updates per second) and the fraction of
+the HBM roofline, FP32 vs FP64, forward and adjoint step, on one GB300.
+
+Workload (default): the 3D relativistic shock on a sphere, 200 x 100 x 100
+cells, inflow beta_x = 0.5, solid sphere r = 15, tau = 0.8, synthetic fields
+from ``workloads.sphere_3d``.  One bench step = one lattice time step (the
+fused stream-and-collide sweep over every cell) of the headline variant, FP32
+deviation storage; the state (608 MB for FP32 A+B) is larger than L2, so no
+flush is needed between steps.  Legs measured in the same run: FP64 forward,
+FP32 / FP64 adjoint step (forward recompute + adjoint kernel).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload (the lattice is not sharded: replicas only); value = all ranks'
+cell updates / max over ranks of the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % of HBM roofline, FP32 vs FP64, forward and adjoint step, 1 GB300"
+FALLBACK_HBM_GBS = 6800.0
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (vector and tensor), nominal
+
+# Algorithmic bytes per lattice update (every population read once and written once).
+BYTES_FWD = {"fp64": 38 * 8 * 2, "fp32": 38 * 4 * 2}
+# Adjoint step: state read (gather), lambda_{t+1} read, lambda_t written.
+BYTES_ADJ = {"fp64": 38 * 8 * 3, "fp32": 38 * 4 * 3}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ----------------------------------------------------------------------------- distributed
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def init_dist(ws, backend):
+    import torch.distributed as dist
+
+    if ws > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def barrier(ws, device=None):
+    if ws > 1:
+        import torch.distributed as dist
+
+        if device is not None and dist.get_backend() == "nccl":
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+def max_over_ranks(value: float, ws: int, device=None) -> float:
+    """Maximum of a per-rank float over all ranks (identity for one rank)."""
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(cells_per_rank: int, steps: int, ms_max: float, ws: int) -> float:
+    """Whole-job MLUPS: every rank's updates over the slowest rank's time."""
+    return cells_per_rank * steps * ws / (ms_max * 1e-3) / 1e6
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling in the background (200 ms)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+        def num(s):
+            try:
+                return float(s)
+            except ValueError:
+                return float("nan")
+
+        sm = np.array([num(r[1]) for r in rows])
+        smax = np.array([num(r[2]) for r in rows])
+        pw = np.array([num(r[3]) for r in rows])
+        load = pw > (np.nanmin(pw) + 0.25 * (np.nanmax(pw) - np.nanmin(pw))) if np.isfinite(pw).any() else sm > 0
+        if load.sum() == 0:
+            load = np.ones_like(sm, bool)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = []
+        for k, nm in enumerate(names):
+            if any(r[5 + k].lower().startswith("active") for r, l in zip(rows, load) if l):
+                reasons.append(nm)
+        return {"sm_mhz": float(np.nanmedian(sm[load])), "sm_max_mhz": float(np.nanmax(smax)), "reasons": reasons,
+                "samples": int(load.sum()), "power_w_max": float(np.nanmax(pw))}
+
+
+# ----------------------------------------------------------------------------- timing legs
+def _events(torch, stream):
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    return a, b
+
+
+def time_forward(sim, steps, warmup, ws, device):
+    """K lattice steps of the context's own state; returns (ms_total, launches)."""
+    import torch
+
+    sim.step(warmup)
+    torch.cuda.synchronize()
+    barrier(ws, device)
+    torch.cuda.synchronize()
+    a, b = _events(torch, sim.stream)
+    l0 = sim.launches
+    a.record(sim.stream)
+    sim.step(steps)
+    b.record(sim.stream)
+    torch.cuda.synchronize()
+    barrier(ws, device)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b), sim.launches - l0
+
+
+def time_adjoint(sim, steps, warmup):
+    """K adjoint steps, each = forward recompute of the state (step_into) plus
+    the adjoint kernel, as the sqrt(T) checkpointed backward pass runs them."""
+    import torch
+
+    s0 = sim.state().clone()
+    s1 = sim.new_state()
+    l_in = torch.zeros_like(s0)
+    l_out = torch.zeros_like(s0)
+    l_in[:, :sim.N].normal_()
+    acc = torch.zeros(4, dtype=torch.float64, device=sim.device)
+
+    def one():
+        sim.step_into(s0, s1)
+        sim.adjoint_step(s0, l_in, l_out, acc[0:1], acc[1:4])
+
+    for _ in range(warmup):
+        one()
+    torch.cuda.synchronize()
+    a, b = _events(torch, sim.stream)
+    l0 = sim.launches
+    a.record(sim.stream)
+    for _ in range(steps):
+        one()
+    b.record(sim.stream)
+    torch.cuda.synchronize()
+    ms_all = a.elapsed_time(b)
+    launches = sim.launches - l0
+    # the adjoint kernel alone (its launch pair)
+    a.record(sim.stream)
+    for _ in range(steps):
+        sim.adjoint_step(s0, l_in, l_out, acc[0:1], acc[1:4])
+    b.record(sim.stream)
+    torch.cuda.synchronize()
+    return ms_all, a.elapsed_time(b), launches
+
+
+def cpu_baseline(w, budget_s=12.0):
+    """The FP64 oracle as it stands, on all host cores, on the full lattice of
+    the workload for as many whole steps as fit in about budget_s seconds."""
+    import oracle
+
+    p = oracle.Params(**w.params())
+    st = oracle.init(p, w.n, w.eps, w.beta, w.solid)
+    oracle.run(p, st, 1, solid=w.solid)  # warm-up
+    t0 = time.time()
+    k = 0
+    while True:
+        oracle.run(p, st, 1, solid=w.solid)
+        k += 1
+        if time.time() - t0 > budget_s and k >= 2:
+            break
+    dt = time.time() - t0
+    return {"value": w.N * k / dt / 1e6, "unit": "MLUPS", "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": f"{k} FP64 oracle steps of the full {w.nx}x{w.ny}x{w.nz} sphere lattice ({dt:.1f} s)"}
+
+
+def e2e_run(w, job_steps, jobs, device):
+    """End to end through the public API: host fields -> rlb_init_fields
+    (H2D) -> job_steps steps -> rlb_macro to host (D2H), FP32."""
+    import torch
+
+    from paper_0912_2913_gb300 import RLB
+
+    sim = RLB.from_workload(w, "fp32", device=device)
+    hn = torch.from_numpy(np.ascontiguousarray(w.n)).pin_memory().numpy()
+    he = torch.from_numpy(np.ascontiguousarray(w.eps)).pin_memory().numpy()
+    hb = torch.from_numpy(np.ascontiguousarray(w.beta)).pin_memory().numpy()
+    hs = torch.from_numpy(np.ascontiguousarray(w.solid)).pin_memory().numpy()
+    sim.init_fields(hn, he, hb, hs).step(20)
+    sim.macro(where="host")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(jobs):
+        sim.init_fields(hn, he, hb, hs)
+        sim.step(job_steps)
+        out = sim.macro(where="host")
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    sim.close()
+    bi = hn.nbytes + he.nbytes + hb.nbytes + hs.nbytes
+    bo = out[0].nbytes + out[1].nbytes + out[2].nbytes
+    return {"value": w.N * job_steps * jobs / dt / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": bi / job_steps,
+            "d2h_bytes_per_step": bo / job_steps,
+            "job": f"{jobs} x (host fields -> init -> {job_steps} FP32 steps -> macro to host)"}
+
+
+def traffic_from_profiles(kernel: str, digest: str):
+    """DRAM bytes per launch from a committed ncu summary, if taken on this build."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        e = d.get(kernel)
+        if e and e.get("build") == digest:
+            return float(e["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+def run_ours(args):
+    import torch
+
+    ws, rank, local = dist_env()
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    init_dist(ws, "nccl")
+    import workloads as W
+    from paper_0912_2913_gb300 import RLB
+    from paper_0912_2913_gb300 import build as B
+
+    w = W.sphere_3d(steps=args.steps)
+    peak, peak_kind = measured_peaks()
+    legs = {}
+    with ClockSampler(local) as clk:
+        # headline leg: FP32 forward
+        sim = RLB.from_workload(w, "fp32", device=device).init_fields(w.n, w.eps, w.beta, w.solid)
+        ms, launches = time_forward(sim, args.steps, args.warmup, ws, device)
+        ms_max = max_over_ranks(ms, ws, device)
+        value = aggregate(w.N, args.steps, ms_max, ws)
+        stats32 = sim.stats()
+        sim.close()
+        per_launch_ms = ms / max(launches, 1)
+        achieved = BYTES_FWD["fp32"] * w.N / (per_launch_ms * 1e-3) / 1e9
+        legs["fp32_forward"] = {"mlups": w.N * args.steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / args.steps,
+                                "bytes_per_update": BYTES_FWD["fp32"], "achieved_gbs": achieved,
+                                "frac_hbm": achieved / peak}
+        if not args.headline_only:
+            sim = RLB.from_workload(w, "fp64", device=device).init_fields(w.n, w.eps, w.beta, w.solid)
+            k64 = max(1, args.steps // 4)
+            ms64, _ = time_forward(sim, k64, max(3, args.warmup // 4), 1, device)
+            a64 = BYTES_FWD["fp64"] * w.N / (ms64 / k64 * 1e-3) / 1e9
+            legs["fp64_forward"] = {"mlups": w.N * k64 / (ms64 * 1e-3) / 1e6, "ms_per_step": ms64 / k64,
+                                    "bytes_per_update": BYTES_FWD["fp64"], "achieved_gbs": a64,
+                                    "frac_hbm": a64 / peak}
+            ka = max(1, k64 // 2)
+            ms_all, ms_k, _ = time_adjoint(sim, ka, 3)
+            legs["fp64_adjoint"] = {"mlups": w.N * ka / (ms_all * 1e-3) / 1e6, "ms_per_step": ms_all / ka,
+                                    "adjoint_kernel_ms": ms_k / ka,
+                                    "ratio_to_forward": (ms_all / ka) / (ms64 / k64),
+                                    "bytes_per_update": BYTES_ADJ["fp64"] + BYTES_FWD["fp64"],
+                                    "frac_hbm": (BYTES_ADJ["fp64"] + BYTES_FWD["fp64"]) * w.N /
+                                    (ms_all / ka * 1e-3) / 1e9 / peak}
+            sim.close()
+            sim = RLB.from_workload(w, "fp32", device=device).init_fields(w.n, w.eps, w.beta, w.solid)
+            sim.step(50)
+            ka = max(1, args.steps // 4)
+            ms_all, ms_k, _ = time_adjoint(sim, ka, 3)
+            legs["fp32_adjoint"] = {"mlups": w.N * ka / (ms_all * 1e-3) / 1e6, "ms_per_step": ms_all / ka,
+                                    "adjoint_kernel_ms": ms_k / ka,
+                                    "ratio_to_forward": (ms_all / ka) / (ms / args.steps),
+                                    "bytes_per_update": BYTES_ADJ["fp32"] + BYTES_FWD["fp32"],
+                                    "frac_hbm": (BYTES_ADJ["fp32"] + BYTES_FWD["fp32"]) * w.N /
+                                    (ms_all / ka * 1e-3) / 1e9 / peak}
+            sim.close()
+    clocks = clk.summary()
+    e2e = None
+    if rank == 0 and not args.no_e2e:
+        e2e = e2e_run(w, args.e2e_steps, 1, device)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, args.cpu_budget)
+    if rank == 0:
+        kern = "k_step_f32"
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "sphere_3d 200x100x100, inflow beta_x=0.5, eps 1/0.1, n 1/0.3, sphere r=15 at "
+                                   "(60,50,50), tau=0.8, FP32 deviation storage (FP64 recovery)",
+                       "cells": w.N, "l2": "state 608 MB > L2 (no flush needed)",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "traffic": traffic_from_profiles(kern, B._digest()), "kernel": kern,
+                         "bytes_per_launch": BYTES_FWD["fp32"] * w.N},
+            "legs": legs,
+            "clocks": clocks,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "gpu_launches": launches,
+            "stats_fp32": stats32,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The FP64 CPU oracle (the reference arm): each step is one oracle step of
+    a bounded sample of the workload (a 10-plane z slab of the sphere lattice)."""
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    import workloads as W
+
+    w = W.sphere_3d()
+    nz = 10
+    z0 = 45
+    sub = W.Workload("sphere_slab", w.nx, w.ny, nz, w.tau, w.c_l, w.xbc, args.steps, w.n[z0:z0 + nz].copy(),
+                     w.eps[z0:z0 + nz].copy(), w.beta[:, z0:z0 + nz].copy(), w.solid[z0:z0 + nz].copy(),
+                     w.n_in, w.eps_in, w.beta_in)
+    p = oracle.Params(**sub.params())
+    st = oracle.init(p, sub.n, sub.eps, sub.beta, sub.solid)
+    oracle.run(p, st, args.warmup, solid=sub.solid)
+    t0 = time.time()
+    oracle.run(p, st, args.steps, solid=sub.solid)
+    dt = time.time() - t0
+    v = sub.N * args.steps / dt / 1e6
+    sample = f"{args.steps} FP64 oracle steps of a 200x100x{nz} z-slab of the sphere lattice"
+    line = {"metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "sphere_3d 200x100x100 (z-slab sample), tau=0.8"},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": oracle.get_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=5000)
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--headline-only", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

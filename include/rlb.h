@@ -1,0 +1,193 @@
+/*
+ * rlb.h -- C ABI of librlb: the relativistic lattice Boltzmann (RLB) step of
+ * Mendoza, Boghosian, Herrmann and Succi, "Lattice Boltzmann scheme for
+ * relativistic fluids" (arXiv:0912.2913), on one NVIDIA GB300 (sm_103a).
+ *
+ * The scheme: two D3Q19 population sets per cell, f_i (particle number) and
+ * g_i (energy-momentum) (Fig. 2 and the paragraph that introduces f_i and
+ * g_i); each step streams the populations one cell along their velocity and
+ * relaxes them to the ultra-relativistic equilibria with BGK time tau
+ * (Eqs. lbe1, lbe2, equil1s, equil2as, equil2bs); the macroscopic fields n,
+ * eps, beta come from the moment constraints n gamma = sum f_i,
+ * (4/3) eps (gamma^2 - 1/4) = sum g_i, (4/3) eps gamma^2 u = sum g_i c_i
+ * with eps = 3P.
+ *
+ * Conventions common to every entry point:
+ *  - Lattice: nx * ny * nz cells, x fastest; cell = (z*ny + y)*nx + x.  y and
+ *    z are periodic; x is periodic, or has ghost planes (rlb_xbc).
+ *  - Field arrays (n, eps, dL/dn, ...) are float64, N = nx*ny*nz values in
+ *    cell order; beta-like arrays are three consecutive planes of N values
+ *    (x, y, z components).  solid is N bytes, non-zero = solid cell.
+ *  - A "state" is one set of populations in device memory: 38 planes
+ *    (f_0..f_18, g_0..g_18), plane q starting at element q * plane_stride
+ *    (rlb_state_layout), element type float64 (RLB_FP64) or float32
+ *    (RLB_FP32_DEV: deviations from the rest equilibrium of n_ref, eps_ref).
+ *    Velocity i follows this order: 0 rest; 1..6 = +x, -x, +y, -y, +z, -z;
+ *    7..18 = (1,1,0), (-1,-1,0), (1,-1,0), (-1,1,0), (1,0,1), (-1,0,-1),
+ *    (1,0,-1), (-1,0,1), (0,1,1), (0,-1,-1), (0,1,-1), (0,-1,1).
+ *    Solid cells hold a NaN-payload marker in every plane.
+ *  - Pointers marked "device" must be device memory of the context's GPU,
+ *    aligned to 16 bytes; the caller owns every array it passes; nothing is
+ *    retained after the call returns (the context keeps only its own
+ *    workspace).  Work is enqueued on the context's CUDA stream; a call
+ *    returns before the GPU finishes unless it says it synchronises.
+ *  - Errors are status codes, never aborts.  A CUDA error is latched in the
+ *    context and returned by every later call on it (rlb_last_error gives the
+ *    text).  Unphysical cells (failed recovery) do not stop a run: values are
+ *    written as computed and the cells are counted (rlb_stats).
+ *  - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef RLB_H
+#define RLB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RLB_API __attribute__((visibility("default")))
+#else
+#define RLB_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rlb_ctx rlb_ctx;
+
+typedef enum {
+    RLB_OK = 0,
+    RLB_ERR_ARG = 1,         /* invalid argument (null pointer, size, parameter range) */
+    RLB_ERR_OOM = 2,         /* a device or host allocation failed                      */
+    RLB_ERR_CUDA = 3,        /* a CUDA call failed; latched in the context              */
+    RLB_ERR_UNPHYSICAL = 4,  /* outputs written, but some cell failed the recovery      */
+    RLB_ERR_STATE = 5        /* call out of order (e.g. step before init)               */
+} rlb_status;
+
+typedef enum { RLB_FP64 = 0, RLB_FP32_DEV = 1 } rlb_precision;
+
+/* x boundary.  Periodic; or an inflow ghost plane x = 0 held at the
+ * equilibrium of (n_in, eps_in, beta_in) plus an outflow ghost x = nx-1 that
+ * copies x = nx-2 after each step; or outflow copies at both ends
+ * (x = 0 <- x = 1, x = nx-1 <- x = nx-2).  Ghost planes are not collided. */
+typedef enum { RLB_BC_PERIODIC = 0, RLB_BC_INFLOW_OUTFLOW = 1, RLB_BC_OUTFLOW_BOTH = 2 } rlb_xbc;
+
+typedef enum { RLB_HOST = 0, RLB_DEVICE = 1 } rlb_where;
+
+typedef struct {
+    int32_t nx, ny, nz;   /* lattice size; nx >= 3 unless periodic; N < 2^31           */
+    int32_t prec;         /* rlb_precision                                              */
+    int32_t xbc;          /* rlb_xbc                                                    */
+    int32_t reserved;     /* must be 0                                                  */
+    double tau;           /* BGK relaxation time in steps, tau > 1/2 (Eqs. lbe1, lbe2)  */
+    double c_l;           /* lattice speed dx/dt in units of c (c_l > 1: "tachyons")    */
+    double n_in, eps_in;  /* inflow state (RLB_BC_INFLOW_OUTFLOW)                       */
+    double beta_in[3];
+    double n_ref, eps_ref;/* RLB_FP32_DEV reference: populations are stored as
+                             f - f^eq(n_ref, eps_ref, beta = 0); must be > 0           */
+} rlb_params;
+
+/* Size of one state: plane stride in elements and element size in bytes;
+ * bytes = 38 * plane_stride * elem_bytes.  The adjoint variables lambda use
+ * the same layout and element type.                                         */
+RLB_API rlb_status rlb_state_layout(const rlb_params* p, int64_t* plane_stride, int32_t* elem_bytes, size_t* bytes);
+
+/* Bytes of device workspace a context needs (two states, counters and
+ * reduction buffers).                                                       */
+RLB_API rlb_status rlb_workspace_bytes(const rlb_params* p, size_t* bytes);
+
+/* Create a context on the current CUDA device.  stream: a cudaStream_t (NULL
+ * = legacy default stream).  workspace: device memory of at least
+ * rlb_workspace_bytes, owned by the caller and kept by the context until
+ * rlb_destroy; or NULL, in which case the context allocates it with
+ * cudaMallocAsync on the stream and frees it in rlb_destroy.
+ * Errors: RLB_ERR_ARG (bad parameters), RLB_ERR_OOM, RLB_ERR_CUDA.        */
+RLB_API rlb_status rlb_create(const rlb_params* p, void* stream, void* workspace, size_t workspace_bytes, rlb_ctx** out);
+RLB_API rlb_status rlb_destroy(rlb_ctx* ctx);
+
+/* Initial condition (the shock-tube paragraph: both sides start as
+ * "thermodynamically equilibrated matter"): every fluid cell starts at
+ * f^eq, g^eq of its fields; the inflow plane at the inflow state; solid
+ * cells take the solid marker.  n, eps: N values; beta: 3N; solid: N bytes
+ * or NULL.  where = RLB_HOST (copied in, synchronises) or RLB_DEVICE.
+ * Solid cells may not lie on the planes x = 0, 1, nx-2, nx-1 of a
+ * non-periodic lattice (RLB_ERR_ARG).  Resets the step counter and stats.  */
+RLB_API rlb_status rlb_init_fields(rlb_ctx* ctx, const double* n, const double* eps, const double* beta,
+                           const uint8_t* solid, rlb_where where);
+
+/* Enqueue nsteps time steps of Eqs. (lbe1), (lbe2) on the context's state
+ * (fused pull streaming with link bounce-back, moments, eps = 3P recovery,
+ * equilibria Eqs. (equil1s, equil2as, equil2bs), BGK relaxation, boundary
+ * planes).  Asynchronous.  nsteps >= 0.                                     */
+RLB_API rlb_status rlb_step(rlb_ctx* ctx, int32_t nsteps);
+
+/* One time step from the device state src into the device state dst (both
+ * caller-owned, rlb_state_layout bytes, distinct); every cell of dst is
+ * written.  Does not touch the context's own state or its statistics.      */
+RLB_API rlb_status rlb_step_into(rlb_ctx* ctx, const void* src, void* dst);
+
+/* Device pointer of the context's current state (valid until the next
+ * rlb_step / rlb_init_fields / rlb_load_state / rlb_destroy).               */
+RLB_API rlb_status rlb_state_ptr(rlb_ctx* ctx, void** state);
+
+/* Copy the current state to / from caller device memory (same layout).     */
+RLB_API rlb_status rlb_save_state(rlb_ctx* ctx, void* dst);
+RLB_API rlb_status rlb_load_state(rlb_ctx* ctx, const void* src);
+
+/* Macroscopic fields of a state (the moment constraints solved with
+ * eps = 3P): n, eps (N values each) and beta (3N); NaN at solid cells.
+ * state = NULL means the context's current state.  where = RLB_DEVICE
+ * (device outputs) or RLB_HOST (host outputs).  Synchronises; returns
+ * RLB_ERR_UNPHYSICAL when a non-solid cell of the state fails the recovery
+ * or the run so far counted an unphysical update (outputs still written).  */
+RLB_API rlb_status rlb_macro(rlb_ctx* ctx, const void* state, double* n, double* eps, double* beta, rlb_where where);
+
+/* Statistics since rlb_init_fields.  Synchronises.  steps: steps taken;
+ * n_unphysical: cell updates whose recovery failed; first_bad: smallest
+ * step*N + cell of such an update, -1 if none; n_nonpositive_eq: cell
+ * updates whose equilibrium had a non-positive population (the positivity
+ * condition c_i.u < c_l^2/3 stated for the tachyon runs, decided in
+ * binary32).  Any pointer may be NULL.                                      */
+RLB_API rlb_status rlb_stats(rlb_ctx* ctx, int64_t* steps, int64_t* n_unphysical, int64_t* first_bad,
+                     int64_t* n_nonpositive_eq);
+
+/* ---- discrete adjoint (transpose of the exact Jacobian of the step) ---- */
+
+/* lambda_T = (d macro / d state)^T (dL/dn, dL/deps, dL/dbeta) at the device
+ * state 'state': device inputs of N, N and 3N float64; lam_out a device
+ * state-layout buffer.  Zero at solid cells.                                */
+RLB_API rlb_status rlb_adjoint_macro(rlb_ctx* ctx, const void* state, const double* dL_dn, const double* dL_deps,
+                             const double* dL_dbeta, void* lam_out);
+
+/* One adjoint step: given the state A_t the forward step started from
+ * (device), lam_in = dL/dA_{t+1} and lam_out = dL/dA_t (device, distinct,
+ * every element written).  Adds dL/dtau of the step to *dL_dtau_accum and
+ * dL/dbeta_in to dL_dbeta_in_accum[3] (device float64; the sums are taken
+ * in a fixed order, so results do not depend on scheduling).               */
+RLB_API rlb_status rlb_adjoint_step(rlb_ctx* ctx, const void* state_t, const void* lam_in, void* lam_out,
+                            double* dL_dtau_accum, double* dL_dbeta_in_accum);
+
+/* Gradient with respect to the initial fields of rlb_init_fields, given
+ * lam0 = dL/dA_0 (device): writes dL/dn0, dL/deps0 (N) and dL/dbeta0 (3N),
+ * zero at solid cells and at the inflow plane, whose dependence on beta_in
+ * is added to dL_dbeta_in_accum[3].  All pointers device.                   */
+RLB_API rlb_status rlb_adjoint_fields(rlb_ctx* ctx, const double* n0, const double* eps0, const double* beta0,
+                              const void* lam0, double* dL_dn0, double* dL_deps0, double* dL_dbeta0,
+                              double* dL_dbeta_in_accum);
+
+/* Wait for the context's stream; returns a latched or new CUDA error.       */
+RLB_API rlb_status rlb_sync(rlb_ctx* ctx);
+
+RLB_API const char* rlb_status_str(rlb_status s);
+
+/* Text of the last error recorded on ctx (or globally when ctx is NULL).    */
+RLB_API const char* rlb_last_error(rlb_ctx* ctx);
+
+/* Number of kernel launches this context has enqueued (for accounting).     */
+RLB_API int64_t rlb_launch_count(rlb_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RLB_H */

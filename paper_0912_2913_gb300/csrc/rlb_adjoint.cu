@@ -1,0 +1,525 @@
+// rlb_adjoint.cu -- discrete adjoint of the relativistic lattice Boltzmann
+// step (the transpose of the exact Jacobian of Eqs. lbe1/lbe2 with the
+// eps = 3P equilibria Eqs. equil1s, equil2as, equil2bs and the closed-form
+// recovery), the adjoint of the macroscopic output and of the equilibrium
+// initialisation.
+//
+// Step adjoint, push form.  With lambda_{t+1} = dL/dA_{t+1}, one thread per
+// interior fluid cell x
+//   1. gathers h(x) from A_t exactly as the forward step does,
+//   2. takes mu(x) = lambda_{t+1}(x) (+ lambda_{t+1} of the outflow ghost that
+//      copies x),
+//   3. forms nu = J_C(h)^T mu, where C(h) = h + (eq(m(h)) - h)/tau:
+//        nu = (1 - 1/tau) mu + (1/tau) P^T (d eq / d m)^T mu,
+//      m = P h the five moments, by the chain rule through the equilibria and
+//      the recovery (the partial derivatives are written out below),
+//   4. scatters nu_i to lambda_t(x - e_i, i), or to lambda_t(x, opp(i)) when
+//      x - e_i is solid (transpose of the pull with bounce-back).
+// Every element of lambda_t has exactly one writer: the scatter above, or
+// the owner cell writing 0 where nobody reads the population (a neighbour
+// that is a ghost plane), or the identity at solid cells (never updated).
+// dL/dtau = sum mu_i (h_i - eq_i)/tau^2 and, at the inflow plane (held at
+// eq(n_in, eps_in, beta_in)), dL/dbeta_in = sum lambda_{t+1} d eq/d beta_in
+// are reduced per block and then over blocks in a fixed order.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rlb_device.cuh"
+
+namespace rlb {
+
+// ---------------------------------------------------------------------------
+// Adjoint of the g equilibria (Eqs. equil2as, equil2bs) with respect to
+// (eps, beta) at fixed mu:   a_eps = sum mu_i d g_i / d eps,
+//                            a_beta = sum mu_i d g_i / d beta.
+// g_{+-p} = w_p [eps/c_l^2 + eps gamma^2 (6 q_p^2 - 2 b2)/c_l^2] +- w_p eps gamma^2 4 q_p / c_l
+// g_0     = w_0 [4 eps gamma^2 - eps (2 + c_l^2)/c_l^2 - 2 eps gamma^2 b2 / c_l^2]
+// with q_p = e_p . beta, b2 = |beta|^2, d gamma^2 / d beta = 2 gamma^4 beta.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void g_eq_adjoint(const T* mug, T eps, T bx, T by, T bz, T b2, T gam2, T inv_cl,
+                                             T inv_cl2, T& a_eps, T& abx, T& aby, T& abz) {
+    const T q[9] = {bx, by, bz, bx + by, bx - by, bx + bz, bx - bz, by + bz, by - bz};
+    T ae = 0, gg2 = 0, gb2 = 0;  // d/d eps, d/d gamma^2, d/d b2 (explicit)
+    T Qp[9];
+    T sw = 0;  // sum_p w_p sigma_p
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        const T w = (T)pair_w(p);
+        const T sig = mug[2 * p + 1] + mug[2 * p + 2];
+        const T del = mug[2 * p + 1] - mug[2 * p + 2];
+        const T sym = (6 * q[p] * q[p] - 2 * b2) * inv_cl2;
+        const T asy = 4 * q[p] * inv_cl;
+        ae += w * (sig * (inv_cl2 + gam2 * sym) + del * gam2 * asy);
+        gg2 += w * (sig * sym + del * asy);
+        sw += w * sig;
+        // d/dq_p: w eps gamma^2 (sigma 12 q / c_l^2 + delta 4 / c_l)
+        Qp[p] = w * (sig * 12 * q[p] * inv_cl2 + del * 4 * inv_cl);
+    }
+    const T w0 = (T)kW0;
+    const T m0 = mug[0];
+    ae += w0 * m0 * (4 * gam2 - (2 * inv_cl2 + 1) - 2 * gam2 * b2 * inv_cl2);
+    gg2 += w0 * m0 * (4 - 2 * b2 * inv_cl2);
+    gb2 = -2 * gam2 * inv_cl2 * (sw + w0 * m0);
+    // chain: gamma^2 (factor eps), b2 (factor eps), q_p (factor eps gamma^2)
+    const T eg = eps * gam2;
+    const T rad = 2 * eps * (gb2 + gam2 * gam2 * gg2);  // coefficient of beta_a
+    a_eps = ae;
+    abx = eg * (Qp[0] + Qp[3] + Qp[4] + Qp[5] + Qp[6]) + rad * bx;
+    aby = eg * (Qp[1] + Qp[3] - Qp[4] + Qp[7] + Qp[8]) + rad * by;
+    abz = eg * (Qp[2] + Qp[5] - Qp[6] + Qp[7] - Qp[8]) + rad * bz;
+}
+
+// Adjoint of the f equilibria written as f_i = w_i S (1 + 3 q_i / c_l) with
+// S = n gamma held fixed: a_S = sum mu_i w_i (1 + 3 q_i/c_l),
+// a_beta = (3 S / c_l) sum_i mu_i w_i e_i.
+template <typename T>
+__device__ __forceinline__ void f_eq_adjoint_S(const T* muf, T S, T bx, T by, T bz, T inv_cl, T& aS, T& abx, T& aby,
+                                               T& abz) {
+    const T q[9] = {bx, by, bz, bx + by, bx - by, bx + bz, bx - bz, by + bz, by - bz};
+    T s0 = (T)kW0 * muf[0], s1 = 0;
+    T d[9];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        const T w = (T)pair_w(p);
+        s0 += w * (muf[2 * p + 1] + muf[2 * p + 2]);
+        d[p] = w * (muf[2 * p + 1] - muf[2 * p + 2]);
+        s1 += d[p] * q[p];
+    }
+    aS = s0 + 3 * inv_cl * s1;
+    const T c = 3 * S * inv_cl;
+    abx = c * (d[0] + d[3] + d[4] + d[5] + d[6]);
+    aby = c * (d[1] + d[3] - d[4] + d[7] + d[8]);
+    abz = c * (d[2] + d[5] - d[6] + d[7] - d[8]);
+}
+
+// Adjoint of the closed-form recovery: given adjoints (a_eps, a_beta) of
+// eps = s - E and beta = 3M/D (s = sqrt(4E^2 - 3M^2), D = 3E + eps), the
+// adjoints of E and M:
+//   d eps/dE = 4E/s - 1,          d eps/dM_b = -3 M_b / s,
+//   d beta_a/dE = -(beta_a/D)(3 + d eps/dE),
+//   d beta_a/dM_b = 3 delta_ab / D + 3 beta_a M_b / (D s).
+template <typename T>
+__device__ __forceinline__ void recovery_adjoint(T a_eps, T abx, T aby, T abz, T E, T s, T D, T bx, T by, T bz, T Mx,
+                                                 T My, T Mz, T& vE, T& vx, T& vy, T& vz) {
+    const T ab_b = abx * bx + aby * by + abz * bz;
+    const T rD = 1 / D;
+    const T rs = 1 / s;
+    const T depsdE = 4 * E * rs - 1;
+    vE = a_eps * depsdE - ab_b * rD * (3 + depsdE);
+    const T c = 3 * rs * (ab_b * rD - a_eps);
+    vx = 3 * abx * rD + c * Mx;
+    vy = 3 * aby * rD + c * My;
+    vz = 3 * abz * rD + c * Mz;
+}
+
+// Block reduction of four doubles into red[blockIdx.x*4 + k].
+__device__ __forceinline__ void block_reduce4(double v0, double v1, double v2, double v3, double* red) {
+    __shared__ double sm[4][32];
+    double v[4] = {v0, v1, v2, v3};
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sm[k][warp] = v[k];
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            double t = lane < nw ? sm[k][lane] : 0.0;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+            if (lane == 0) red[blockIdx.x * 4 + k] = t;
+        }
+    }
+}
+
+// Sum the per-block partials in block order and add them to the accumulators.
+__global__ void k_finalize(const double* __restrict__ red, int nblocks, double* dtau, double* dbeta_in) {
+    __shared__ double sm[4][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;  // 128 threads: warp k reduces component k
+    double t = 0.0;
+    for (int b = lane; b < nblocks; b += 32) t += red[b * 4 + warp];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+    if (lane == 0) sm[warp][0] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (dtau) *dtau += sm[0][0];
+        if (dbeta_in) {
+            dbeta_in[0] += sm[1][0];
+            dbeta_in[1] += sm[2][0];
+            dbeta_in[2] += sm[3][0];
+        }
+    }
+}
+
+// Adjoint of eq(n, eps, beta) with respect to the fields (f with n gamma,
+// gamma = (1 - b2)^-1/2, d gamma / d beta = gamma^3 beta).
+__device__ void eq_fields_adjoint(const double* muf, const double* mug, double n, double eps, double bx, double by,
+                                  double bz, const Phys& ph, double& an, double& ae, double& abx, double& aby,
+                                  double& abz) {
+    const double b2 = bx * bx + by * by + bz * bz;
+    const double gam2 = 1.0 / (1.0 - b2);
+    const double gam = sqrt(gam2);
+    double aS, fbx, fby, fbz;
+    f_eq_adjoint_S(muf, n * gam, bx, by, bz, ph.inv_cl, aS, fbx, fby, fbz);
+    // S = n gamma: dS/dn = gamma, dS/dbeta = n gamma^3 beta
+    an = aS * gam;
+    const double cS = aS * n * gam * gam2;
+    double gbx, gby, gbz;
+    g_eq_adjoint(mug, eps, bx, by, bz, b2, gam2, ph.inv_cl, ph.inv_cl2, ae, gbx, gby, gbz);
+    abx = fbx + gbx + cS * bx;
+    aby = fby + gby + cS * by;
+    abz = fbz + gbz + cS * bz;
+}
+
+// ---------------------------------------------------------------------------
+// Step adjoint (T = double: FP64 states; T = float: FP32 deviation states,
+// recovery in FP64, adjoint arithmetic in FP32).
+// ---------------------------------------------------------------------------
+template <typename T, int XBC>
+__global__ void __launch_bounds__(128) k_adjoint_step(const T* __restrict__ A, const T* __restrict__ Lin,
+                                                      T* __restrict__ Lout, Geom g, Phys ph, double* red) {
+    const long long S = g.S;
+    double tau_acc = 0.0, bin0 = 0.0, bin1 = 0.0, bin2 = 0.0;
+    const double inv_tau2 = ph.omega * ph.omega;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < g.N; idx += gridDim.x * blockDim.x) {
+        int x, y, z;
+        cell_coords(g, idx, x, y, z);
+        const bool ghost = (XBC != XBC_PERIODIC) && (x == 0 || x == g.nx - 1);
+        if (ghost) {
+            // Nobody reads the ghost's populations that do not point into the
+            // lattice; the others are written by the scatter of x +- 1.
+            const int inward = (x == 0) ? 1 : -1;
+#pragma unroll
+            for (int i = 0; i < 19; ++i) {
+                if (vel_x(i) != inward) {
+                    Lout[i * S + idx] = (T)0;
+                    Lout[(19 + i) * S + idx] = (T)0;
+                }
+            }
+            if (XBC == XBC_INFLOW_OUTFLOW && x == 0 && !is_solid(A[idx])) {
+                double lf[19], lg[19];
+#pragma unroll
+                for (int i = 0; i < 19; ++i) {
+                    lf[i] = (double)Lin[i * S + idx];
+                    lg[i] = (double)Lin[(19 + i) * S + idx];
+                }
+                double an, ae, ax, ay, az;
+                eq_fields_adjoint(lf, lg, ph.n_in, ph.eps_in, ph.beta_in[0], ph.beta_in[1], ph.beta_in[2], ph, an,
+                                  ae, ax, ay, az);
+                bin0 += ax;
+                bin1 += ay;
+                bin2 += az;
+            }
+            continue;
+        }
+        if (is_solid(A[idx])) {  // never updated: identity
+#pragma unroll
+            for (int q = 0; q < 38; ++q) Lout[q * S + idx] = Lin[q * S + idx];
+            continue;
+        }
+        const PullOffsets o(g, x, y, z);
+        T h[38];
+        bool bounced[19];
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            const int s = idx + o.src(i);
+            h[i] = A[i * S + s];
+            h[19 + i] = A[(19 + i) * S + s];
+            bounced[i] = false;
+        }
+#pragma unroll
+        for (int i = 1; i < 19; ++i) {
+            if (is_solid(h[i])) {
+                bounced[i] = true;
+                h[i] = A[opp(i) * S + idx];
+                h[19 + i] = A[(19 + opp(i)) * S + idx];
+            }
+        }
+        T mu[38];
+#pragma unroll
+        for (int q = 0; q < 38; ++q) mu[q] = Lin[q * S + idx];
+        if (XBC != XBC_PERIODIC && x == g.nx - 2) {
+#pragma unroll
+            for (int q = 0; q < 38; ++q) mu[q] += Lin[q * S + idx + 1];
+        }
+        if (XBC == XBC_OUTFLOW_BOTH && x == 1) {
+#pragma unroll
+            for (int q = 0; q < 38; ++q) mu[q] += Lin[q * S + idx - 1];
+        }
+        // ---- forward recompute: moments and recovery in FP64 ----
+        T sfT, ET, mxT, myT, mzT;
+        {
+            T d[9];
+            T s = h[0];
+#pragma unroll
+            for (int i = 1; i < 19; ++i) s += h[i];
+            T es = h[19];
+#pragma unroll
+            for (int p = 0; p < 9; ++p) {
+                es += h[20 + 2 * p] + h[21 + 2 * p];
+                d[p] = h[20 + 2 * p] - h[21 + 2 * p];
+            }
+            sfT = s;
+            ET = es;
+            mxT = d[0] + d[3] + d[4] + d[5] + d[6];
+            myT = d[1] + d[3] - d[4] + d[7] + d[8];
+            mzT = d[2] + d[5] - d[6] + d[7] - d[8];
+        }
+        double sf = (double)sfT, E = (double)ET;
+        if (sizeof(T) == 4) {
+            sf += ph.n_ref;
+            E += ph.eps_ref;
+        }
+        const double Mx = (double)mxT * ph.c_l, My = (double)myT * ph.c_l, Mz = (double)mzT * ph.c_l;
+        const double sq = sqrt(4.0 * E * E - 3.0 * (Mx * Mx + My * My + Mz * Mz));
+        const double eps = sq - E;
+        const double D = 3.0 * E + eps;
+        const double r3 = 3.0 / D;
+        const double bx = Mx * r3, by = My * r3, bz = Mz * r3;
+        const double b2 = bx * bx + by * by + bz * bz;
+        const double gam2 = 1.0 / (1.0 - b2);
+        // ---- equilibria (as stored: FP64 values or FP32 deviations) ----
+        T feq[19], geq[19];
+        {
+            const double q[9] = {bx, by, bz, bx + by, bx - by, bx + bz, bx - bz, by + bz, by - bz};
+            const double eg = eps * gam2;
+            if (sizeof(T) == 8) {
+                feq[0] = (T)(kW0 * sf);
+                geq[0] = (T)(kW0 * (4.0 * eg - eps * (2.0 * ph.inv_cl2 + 1.0) - 2.0 * eg * b2 * ph.inv_cl2));
+            } else {
+                feq[0] = (T)(kW0 * (double)sfT);
+                geq[0] = (T)(kW0 * ((eps - ph.eps_ref) * (3.0 - 2.0 * ph.inv_cl2) + eg * b2 * (4.0 - 2.0 * ph.inv_cl2)));
+            }
+#pragma unroll
+            for (int p = 0; p < 9; ++p) {
+                const double w = pair_w(p);
+                const double fb = (sizeof(T) == 8) ? sf : (double)sfT;
+                const double fa = 3.0 * sf * q[p] * ph.inv_cl;
+                feq[2 * p + 1] = (T)(w * (fb + fa));
+                feq[2 * p + 2] = (T)(w * (fb - fa));
+                const double e0 = (sizeof(T) == 8) ? eps : (eps - ph.eps_ref);
+                const double gs = (e0 + eg * (6.0 * q[p] * q[p] - 2.0 * b2)) * ph.inv_cl2;
+                const double ga = 4.0 * eg * q[p] * ph.inv_cl;
+                geq[2 * p + 1] = (T)(w * (gs + ga));
+                geq[2 * p + 2] = (T)(w * (gs - ga));
+            }
+        }
+        // dL/dtau: sum mu (h - eq) / tau^2
+        {
+            T acc = 0;
+#pragma unroll
+            for (int i = 0; i < 19; ++i) acc += mu[i] * (h[i] - feq[i]) + mu[19 + i] * (h[19 + i] - geq[i]);
+            tau_acc += (double)acc * inv_tau2;
+        }
+        // ---- nu = J_C^T mu ----
+        T aS, fbx, fby, fbz, ae, gbx, gby, gbz;
+        f_eq_adjoint_S<T>(mu, (T)sf, (T)bx, (T)by, (T)bz, (T)ph.inv_cl, aS, fbx, fby, fbz);
+        g_eq_adjoint<T>(mu + 19, (T)eps, (T)bx, (T)by, (T)bz, (T)b2, (T)gam2, (T)ph.inv_cl, (T)ph.inv_cl2, ae, gbx,
+                        gby, gbz);
+        T vE, vx, vy, vz;
+        recovery_adjoint<T>(ae, fbx + gbx, fby + gby, fbz + gbz, (T)E, (T)sq, (T)D, (T)bx, (T)by, (T)bz, (T)Mx,
+                            (T)My, (T)Mz, vE, vx, vy, vz);
+        const T om = (T)ph.omega, omw = (T)(1.0 - ph.omega);
+        const T cl = (T)ph.c_l;
+        T nu[38];
+        const T nuS = om * aS;
+        const T nuE = om * vE;
+        nu[0] = omw * mu[0] + nuS;
+        nu[19] = omw * mu[19] + nuE;
+        {
+            const T pm[9] = {vx, vy, vz, vx + vy, vx - vy, vx + vz, vx - vz, vy + vz, vy - vz};
+#pragma unroll
+            for (int p = 0; p < 9; ++p) {
+                nu[2 * p + 1] = omw * mu[2 * p + 1] + nuS;
+                nu[2 * p + 2] = omw * mu[2 * p + 2] + nuS;
+                const T t = om * cl * pm[p];
+                nu[20 + 2 * p] = omw * mu[20 + 2 * p] + nuE + t;
+                nu[21 + 2 * p] = omw * mu[21 + 2 * p] + nuE - t;
+            }
+        }
+        // ---- scatter: transpose of the pull with bounce-back ----
+        Lout[idx] = nu[0];
+        Lout[19 * S + idx] = nu[19];
+#pragma unroll
+        for (int i = 1; i < 19; ++i) {
+            if (bounced[i]) {
+                Lout[opp(i) * S + idx] = nu[i];
+                Lout[(19 + opp(i)) * S + idx] = nu[19 + i];
+            } else {
+                const int s = idx + o.src(i);
+                Lout[i * S + s] = nu[i];
+                Lout[(19 + i) * S + s] = nu[19 + i];
+            }
+        }
+        // populations of x that a ghost plane would pull: nobody reads them
+        if (XBC != XBC_PERIODIC && (x == 1 || x == g.nx - 2)) {
+#pragma unroll
+            for (int i = 1; i < 19; ++i) {
+                const bool to_ghost = (x == 1 && vel_x(i) == -1) || (x == g.nx - 2 && vel_x(i) == 1);
+                if (to_ghost) {
+                    Lout[i * S + idx] = (T)0;
+                    Lout[(19 + i) * S + idx] = (T)0;
+                }
+            }
+        }
+    }
+    block_reduce4(tau_acc, bin0, bin1, bin2, red);
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint of the macroscopic output: n = S sqrt(1 - b2), eps, beta.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(128) k_adjoint_macro(const T* __restrict__ A, const double* __restrict__ dn,
+                                                       const double* __restrict__ deps, const double* __restrict__ dbeta,
+                                                       T* __restrict__ lam, Geom g, Phys ph) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= g.N) return;
+    const long long S = g.S;
+    if (is_solid(A[idx])) {
+        for (int q = 0; q < 38; ++q) lam[q * S + idx] = (T)0;
+        return;
+    }
+    double h[38];
+    for (int q = 0; q < 38; ++q) h[q] = (double)A[q * S + idx];
+    double sf = 0, E = 0, Mx = 0, My = 0, Mz = 0;
+    for (int i = 0; i < 19; ++i) {
+        sf += h[i];
+        E += h[19 + i];
+        Mx += h[19 + i] * vel_x(i);
+        My += h[19 + i] * vel_y(i);
+        Mz += h[19 + i] * vel_z(i);
+    }
+    if (sizeof(T) == 4) {
+        sf += ph.n_ref;
+        E += ph.eps_ref;
+    }
+    Mx *= ph.c_l;
+    My *= ph.c_l;
+    Mz *= ph.c_l;
+    const double sq = sqrt(4.0 * E * E - 3.0 * (Mx * Mx + My * My + Mz * Mz));
+    const double eps = sq - E;
+    const double D = 3.0 * E + eps;
+    const double bx = 3.0 * Mx / D, by = 3.0 * My / D, bz = 3.0 * Mz / D;
+    const double b2 = bx * bx + by * by + bz * bz;
+    const double rt = sqrt(1.0 - b2);
+    const double gdn = dn[idx];
+    const double aS = gdn * rt;
+    const double c = -gdn * sf / rt;
+    const double abx = dbeta[idx] + c * bx;
+    const double aby = dbeta[g.N + idx] + c * by;
+    const double abz = dbeta[2 * (long long)g.N + idx] + c * bz;
+    double vE, vx, vy, vz;
+    recovery_adjoint<double>(deps[idx], abx, aby, abz, E, sq, D, bx, by, bz, Mx, My, Mz, vE, vx, vy, vz);
+    for (int i = 0; i < 19; ++i) {
+        lam[i * S + idx] = (T)aS;
+        lam[(19 + i) * S + idx] = (T)(vE + ph.c_l * (vel_x(i) * vx + vel_y(i) * vy + vel_z(i) * vz));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint of the initialisation A_0 = eq(n0, eps0, beta0).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(128) k_adjoint_fields(const double* __restrict__ n0, const double* __restrict__ e0,
+                                                        const double* __restrict__ b0, const T* __restrict__ A0,
+                                                        const T* __restrict__ lam, double* __restrict__ dn,
+                                                        double* __restrict__ de, double* __restrict__ db, Geom g,
+                                                        Phys ph, double* red) {
+    const long long S = g.S;
+    double bin0 = 0.0, bin1 = 0.0, bin2 = 0.0;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < g.N; idx += gridDim.x * blockDim.x) {
+        const int x = idx % g.nx;
+        double lf[19], lg[19];
+        double an = 0, ae = 0, ax = 0, ay = 0, az = 0;
+        const bool solid = is_solid(A0[idx]);
+        if (!solid) {
+            for (int i = 0; i < 19; ++i) {
+                lf[i] = (double)lam[i * S + idx];
+                lg[i] = (double)lam[(19 + i) * S + idx];
+            }
+            if (g.xbc == XBC_INFLOW_OUTFLOW && x == 0) {
+                eq_fields_adjoint(lf, lg, ph.n_in, ph.eps_in, ph.beta_in[0], ph.beta_in[1], ph.beta_in[2], ph, an,
+                                  ae, ax, ay, az);
+                bin0 += ax;
+                bin1 += ay;
+                bin2 += az;
+                an = ae = ax = ay = az = 0;
+            } else {
+                eq_fields_adjoint(lf, lg, n0[idx], e0[idx], b0[idx], b0[g.N + idx], b0[2 * (long long)g.N + idx], ph,
+                                  an, ae, ax, ay, az);
+            }
+        }
+        dn[idx] = an;
+        de[idx] = ae;
+        db[idx] = ax;
+        db[g.N + idx] = ay;
+        db[2 * (long long)g.N + idx] = az;
+    }
+    block_reduce4(0.0, bin0, bin1, bin2, red);
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+static inline int adj_blocks(int N) {
+    const int need = (N + 127) / 128;
+    return need < kAdjBlocksMax ? need : kAdjBlocksMax;
+}
+
+cudaError_t launch_adjoint_macro(int prec, const Geom& g, const Phys& ph, const void* A, const double* dn,
+                                 const double* deps, const double* dbeta, void* lam, cudaStream_t st) {
+    const unsigned nb = (unsigned)((g.N + 127) / 128);
+    set_last_launch_count(1);
+    if (prec == 0)
+        k_adjoint_macro<double><<<nb, 128, 0, st>>>((const double*)A, dn, deps, dbeta, (double*)lam, g, ph);
+    else
+        k_adjoint_macro<float><<<nb, 128, 0, st>>>((const float*)A, dn, deps, dbeta, (float*)lam, g, ph);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static void adjoint_step_t(const Geom& g, const Phys& ph, const T* A, const T* Li, T* Lo, double* red, int nb,
+                           cudaStream_t st) {
+    switch (g.xbc) {
+        case XBC_PERIODIC: k_adjoint_step<T, XBC_PERIODIC><<<nb, 128, 0, st>>>(A, Li, Lo, g, ph, red); break;
+        case XBC_INFLOW_OUTFLOW: k_adjoint_step<T, XBC_INFLOW_OUTFLOW><<<nb, 128, 0, st>>>(A, Li, Lo, g, ph, red); break;
+        default: k_adjoint_step<T, XBC_OUTFLOW_BOTH><<<nb, 128, 0, st>>>(A, Li, Lo, g, ph, red); break;
+    }
+}
+
+cudaError_t launch_adjoint_step(int prec, const Geom& g, const Phys& ph, const void* A, const void* lam_in,
+                                void* lam_out, double* red, double* dtau, double* dbeta_in, cudaStream_t st) {
+    const int nb = adj_blocks(g.N);
+    set_last_launch_count(2);
+    if (prec == 0)
+        adjoint_step_t<double>(g, ph, (const double*)A, (const double*)lam_in, (double*)lam_out, red, nb, st);
+    else
+        adjoint_step_t<float>(g, ph, (const float*)A, (const float*)lam_in, (float*)lam_out, red, nb, st);
+    k_finalize<<<1, 128, 0, st>>>(red, nb, dtau, dbeta_in);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_fields(int prec, const Geom& g, const Phys& ph, const double* n0, const double* eps0,
+                                  const double* beta0, const void* A0, const void* lam0, double* dn0, double* deps0,
+                                  double* dbeta0, double* red, double* dbeta_in, cudaStream_t st) {
+    const int nb = adj_blocks(g.N);
+    set_last_launch_count(2);
+    if (prec == 0)
+        k_adjoint_fields<double><<<nb, 128, 0, st>>>(n0, eps0, beta0, (const double*)A0, (const double*)lam0, dn0,
+                                                     deps0, dbeta0, g, ph, red);
+    else
+        k_adjoint_fields<float><<<nb, 128, 0, st>>>(n0, eps0, beta0, (const float*)A0, (const float*)lam0, dn0, deps0,
+                                                    dbeta0, g, ph, red);
+    k_finalize<<<1, 128, 0, st>>>(red, nb, nullptr, dbeta_in);
+    return cudaGetLastError();
+}
+
+}  // namespace rlb

@@ -1,0 +1,137 @@
+// rlb_device.cuh -- device-side building blocks of librlb's kernels.
+//
+// D3Q19 velocity set of the paper (Fig. 2: one rest velocity, six of speed
+// c_l, twelve of speed sqrt(2) c_l; weights 1/3, 1/18, 1/36), written for the
+// kernels in opposite pairs: velocity 2p+1 is e_p below and velocity 2p+2 is
+// -e_p (p = 0..8), velocity 0 is at rest.  The population planes of a state
+// follow this order (documented in include/rlb.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rlb_internal.h"
+
+namespace rlb {
+
+// e_p of the nine pairs: +x, +y, +z, (1,1,0), (1,-1,0), (1,0,1), (1,0,-1), (0,1,1), (0,1,-1).
+__host__ __device__ constexpr int pair_ex(int p) { return (p == 0 || (p >= 3 && p <= 6)) ? 1 : 0; }
+__host__ __device__ constexpr int pair_ey(int p) {
+    return (p == 1 || p == 3 || p == 7 || p == 8) ? 1 : (p == 4 ? -1 : 0);
+}
+__host__ __device__ constexpr int pair_ez(int p) {
+    return (p == 2 || p == 5 || p == 7) ? 1 : ((p == 6 || p == 8) ? -1 : 0);
+}
+// Velocity i (0..18) as integers.
+__host__ __device__ constexpr int vel_x(int i) { return i == 0 ? 0 : ((i & 1) ? pair_ex((i - 1) >> 1) : -pair_ex((i - 1) >> 1)); }
+__host__ __device__ constexpr int vel_y(int i) { return i == 0 ? 0 : ((i & 1) ? pair_ey((i - 1) >> 1) : -pair_ey((i - 1) >> 1)); }
+__host__ __device__ constexpr int vel_z(int i) { return i == 0 ? 0 : ((i & 1) ? pair_ez((i - 1) >> 1) : -pair_ez((i - 1) >> 1)); }
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+// Pair weight: 1/18 for the axis pairs (speed c_l), 1/36 for the diagonal pairs.
+__host__ __device__ constexpr double pair_w(int p) { return p < 3 ? 1.0 / 18.0 : 1.0 / 36.0; }
+constexpr double kW0 = 1.0 / 3.0;
+
+// Solid cells carry a quiet-NaN marker with a payload in every plane; the
+// arithmetic of a step never produces these payloads.  A pulled value equal
+// to the marker means "the neighbour is solid" (link bounce-back).
+constexpr unsigned long long kSolidBits64 = 0x7FF8D0D05011D000ull;
+constexpr unsigned int kSolidBits32 = 0x7FC5011Du;
+
+__device__ __forceinline__ bool is_solid(double v) {
+    return (unsigned long long)__double_as_longlong(v) == kSolidBits64;
+}
+__device__ __forceinline__ bool is_solid(float v) { return __float_as_uint(v) == kSolidBits32; }
+__device__ __forceinline__ double solid_marker_d() { return __longlong_as_double((long long)kSolidBits64); }
+__device__ __forceinline__ float solid_marker_f() { return __uint_as_float(kSolidBits32); }
+
+// Finite and > 0 / finite and >= 0, on the bit pattern (no FP64 pipe work).
+__device__ __forceinline__ bool pos_finite(double v) {
+    long long b = __double_as_longlong(v);
+    return b > 0 && b < 0x7FF0000000000000ll;
+}
+__device__ __forceinline__ bool nonneg_finite(double v) {
+    long long b = __double_as_longlong(v);
+    return (b >= 0 && b < 0x7FF0000000000000ll) || b == (long long)0x8000000000000000ull;
+}
+// 0 <= v < 1 (v is a sum of squares).
+__device__ __forceinline__ bool below_one(double v) {
+    long long b = __double_as_longlong(v);
+    return b >= 0 && b < 0x3FF0000000000000ll;
+}
+
+// Offsets (in cells) from cell (x, y, z) to the source x - e of a pull, for
+// the components -1 / 0 / +1 of e, with periodic wrap.  For a non-periodic x
+// the interior cells never wrap, so the same formula serves every case.
+struct PullOffsets {
+    int xm, xp, ym, yp, zm, zp;  // source at x-1 / x+1, y-1 / y+1, z-1 / z+1
+
+    __device__ __forceinline__ PullOffsets(const Geom& g, int x, int y, int z) {
+        xm = (x == 0) ? g.nx - 1 : -1;
+        xp = (x == g.nx - 1) ? -(g.nx - 1) : 1;
+        ym = (y == 0) ? (g.ny - 1) * g.nx : -g.nx;
+        yp = (y == g.ny - 1) ? -(g.ny - 1) * g.nx : g.nx;
+        zm = (z == 0) ? (g.nz - 1) * g.nxy : -g.nxy;
+        zp = (z == g.nz - 1) ? -(g.nz - 1) * g.nxy : g.nxy;
+    }
+    // Offset of the source cell x - e_i of velocity i.
+    __device__ __forceinline__ int src(int i) const {
+        const int ex = vel_x(i), ey = vel_y(i), ez = vel_z(i);
+        return (ex > 0 ? xm : (ex < 0 ? xp : 0)) + (ey > 0 ? ym : (ey < 0 ? yp : 0)) +
+               (ez > 0 ? zm : (ez < 0 ? zp : 0));
+    }
+    // Offset of the destination x + e_i (the cell that pulls velocity i from x).
+    __device__ __forceinline__ int dst(int i) const {
+        const int ex = vel_x(i), ey = vel_y(i), ez = vel_z(i);
+        return (ex > 0 ? xp : (ex < 0 ? xm : 0)) + (ey > 0 ? yp : (ey < 0 ? ym : 0)) +
+               (ez > 0 ? zp : (ez < 0 ? zm : 0));
+    }
+};
+
+__device__ __forceinline__ void cell_coords(const Geom& g, int idx, int& x, int& y, int& z) {
+    const int yz = idx / g.nx;
+    x = idx - yz * g.nx;
+    z = yz / g.ny;
+    y = yz - z * g.ny;
+}
+
+// Warp-aggregated statistics: each warp adds its counts to one of
+// kCounterSlots slots, so no address sees much contention.
+__device__ __forceinline__ void count_flags(const Counters& c, bool unphys, bool nonpos, unsigned long long bad_id) {
+    const unsigned act = __activemask();
+    const unsigned mu = __ballot_sync(act, unphys);
+    const unsigned mp = __ballot_sync(act, nonpos);
+    if ((mu | mp) == 0u) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(act) - 1;
+    if (unphys) atomicMin(c.first_bad, bad_id);
+    if (lane == leader) {
+        const unsigned slot = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) & (kCounterSlots - 1);
+        if (mu) atomicAdd(c.slots + slot, (unsigned long long)__popc(mu));
+        if (mp) atomicAdd(c.slots + kCounterSlots + slot, (unsigned long long)__popc(mp));
+    }
+}
+
+// Positivity of the equilibria (the condition c_i . u < c_l^2/3 stated for the
+// tachyon runs, with the matching g-bracket of Eq. equil2as), decided in
+// binary32 on beta rounded to binary32, every operation rounded on its own
+// (no contraction):  flag when, for some direction pair with q = e_p.beta,
+//   c_l - 3|q| <= 0   or   (1 - 3 b2) + |q| (6|q| - 4 c_l) <= 0,
+// with b2 = (bx*bx + by*by) + bz*bz.
+__device__ __forceinline__ bool nonpositive_eq(float bx, float by, float bz, float cl) {
+    const float q[9] = {bx, by, bz, __fadd_rn(bx, by), __fsub_rn(bx, by), __fadd_rn(bx, bz),
+                        __fsub_rn(bx, bz), __fadd_rn(by, bz), __fsub_rn(by, bz)};
+    const float b2 = __fadd_rn(__fadd_rn(__fmul_rn(bx, bx), __fmul_rn(by, by)), __fmul_rn(bz, bz));
+    const float c0 = __fsub_rn(1.0f, __fmul_rn(3.0f, b2));
+    const float four_cl = __fmul_rn(4.0f, cl);
+    bool flag = false;
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        const float aq = fabsf(q[p]);
+        const float fb = __fsub_rn(cl, __fmul_rn(3.0f, aq));
+        const float gb = __fadd_rn(c0, __fmul_rn(aq, __fsub_rn(__fmul_rn(6.0f, aq), four_cl)));
+        flag |= (fb <= 0.0f) | (gb <= 0.0f);
+    }
+    return flag;
+}
+
+}  // namespace rlb

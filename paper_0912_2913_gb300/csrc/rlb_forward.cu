@@ -1,0 +1,497 @@
+// rlb_forward.cu -- forward kernels of librlb: the fused stream-and-collide
+// step of the relativistic lattice Boltzmann scheme (Eqs. lbe1, lbe2 with the
+// eps = 3P equilibria Eqs. equil1s, equil2as, equil2bs), the equilibrium
+// initialisation and the macroscopic output.
+//
+// One thread owns one cell.  A step pulls the 38 populations that arrive at
+// the cell (h_i(x) = A_i(x - e_i), link bounce-back h_i(x) = A_opp(i)(x) when
+// x - e_i is solid), forms the five moments, recovers (n gamma, eps, beta) in
+// closed form, builds the equilibria pair by pair (velocities i and opp(i)
+// share every term but the odd one) and writes the BGK-relaxed populations
+// B_i = h_i + (eq_i - h_i)/tau.  State planes are structure-of-arrays, so a
+// warp's loads and stores of one plane are 32 consecutive elements (the x
+// neighbours are off by one element and share cache sectors).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rlb_device.cuh"
+
+namespace rlb {
+
+namespace {
+int g_last_launches = 0;
+}
+int last_launch_count() { return g_last_launches; }
+void set_last_launch_count(int n) { g_last_launches = n; }
+
+// ---------------------------------------------------------------------------
+// Moments in pair form: S = sum f, E = sum g, M = c_l sum g e.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void moments_pairs(const T* f, const T* g, T& sf, T& e, T& mx, T& my, T& mz) {
+    T s = f[0];
+#pragma unroll
+    for (int i = 1; i < 19; ++i) s += f[i];
+    T d[9];
+    T es = g[0];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        es += g[2 * p + 1] + g[2 * p + 2];
+        d[p] = g[2 * p + 1] - g[2 * p + 2];
+    }
+    sf = s;
+    e = es;
+    mx = d[0] + d[3] + d[4] + d[5] + d[6];
+    my = d[1] + d[3] - d[4] + d[7] + d[8];
+    mz = d[2] + d[5] - d[6] + d[7] - d[8];
+}
+
+// ---------------------------------------------------------------------------
+// FP64 step.
+// ---------------------------------------------------------------------------
+template <int XBC, bool SOLID>
+__global__ void __launch_bounds__(128) k_step_f64(const double* __restrict__ A, double* __restrict__ B, Geom g,
+                                                  Phys ph, Counters cnt, int count, long long step_index) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= g.N) return;
+    int x, y, z;
+    cell_coords(g, idx, x, y, z);
+    const long long S = g.S;
+    if (XBC != XBC_PERIODIC && (x == 0 || x == g.nx - 1)) {
+        // Ghost planes are not collided.  The inflow plane keeps its fixed
+        // equilibrium (copied so that every cell of B is written); outflow
+        // ghosts are written by the cell they copy.
+        if (XBC == XBC_INFLOW_OUTFLOW && x == 0) {
+#pragma unroll
+            for (int q = 0; q < 38; ++q) B[q * S + idx] = __ldg(A + q * S + idx);
+        }
+        return;
+    }
+    const PullOffsets o(g, x, y, z);
+    double f[19], gg[19];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const int s = idx + o.src(i);
+        f[i] = __ldg(A + i * S + s);
+        gg[i] = __ldg(A + (19 + i) * S + s);
+    }
+    if (SOLID) {
+        if (is_solid(f[0])) {  // the cell itself is solid: keep the marker
+            const double m = solid_marker_d();
+#pragma unroll
+            for (int q = 0; q < 38; ++q) B[q * S + idx] = m;
+            return;
+        }
+#pragma unroll
+        for (int i = 1; i < 19; ++i) {
+            if (is_solid(f[i])) {  // link bounce-back
+                f[i] = __ldg(A + opp(i) * S + idx);
+                gg[i] = __ldg(A + (19 + opp(i)) * S + idx);
+            }
+        }
+    }
+    double sf, E, mx, my, mz;
+    moments_pairs(f, gg, sf, E, mx, my, mz);
+    mx *= ph.c_l;
+    my *= ph.c_l;
+    mz *= ph.c_l;
+    // Recovery with eps = 3P: eps = -E + sqrt(4E^2 - 3M^2), beta = 3M/(3E + eps).
+    const double m2 = mx * mx + my * my + mz * mz;
+    const double disc = 4.0 * E * E - 3.0 * m2;
+    const double eps = sqrt(disc) - E;
+    const double r3 = 3.0 / (3.0 * E + eps);
+    const double bx = mx * r3, by = my * r3, bz = mz * r3;
+    const double b2 = bx * bx + by * by + bz * bz;
+    const double gam2 = 1.0 / (1.0 - b2);
+    const bool unphys = !(pos_finite(sf) && pos_finite(E) && nonneg_finite(disc) && pos_finite(eps) && below_one(b2));
+    const bool nonpos = nonpositive_eq((float)bx, (float)by, (float)bz, (float)ph.c_l);
+
+    const double om = ph.omega, omw = 1.0 - ph.omega;
+    const double q[9] = {bx, by, bz, bx + by, bx - by, bx + bz, bx - bz, by + bz, by - bz};
+    // f^eq_i = w_i S_f (1 + 3 q_i / c_l)     (Eq. equil1s with n gamma = S_f)
+    const double fs1 = om * (1.0 / 18.0) * sf, fs2 = om * (1.0 / 36.0) * sf;
+    const double fa = 3.0 * om * sf * ph.inv_cl;
+    // g^eq_i = w_i [eps/c_l^2 + eps gamma^2 (6 q^2/c_l^2 - 2 b2/c_l^2)] +- w_i eps gamma^2 4 q / c_l
+    const double eg = eps * gam2;
+    const double k1 = om * (eps - 2.0 * eg * b2) * ph.inv_cl2;
+    const double k2 = 6.0 * om * eg * ph.inv_cl2;
+    const double k3 = 4.0 * om * eg * ph.inv_cl;
+    double outf[19], outg[19];
+    outf[0] = fma(omw, f[0], om * kW0 * sf);
+    // g_0^eq = w_0 [4 eps gamma^2 - eps (2 + c_l^2)/c_l^2 - 2 eps gamma^2 b2/c_l^2]   (Eq. equil2bs)
+    const double g0eq = kW0 * (4.0 * eg - eps * (2.0 * ph.inv_cl2 + 1.0) - 2.0 * eg * b2 * ph.inv_cl2);
+    outg[0] = fma(omw, gg[0], om * g0eq);
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        const double w = pair_w(p);
+        const double fsym = p < 3 ? fs1 : fs2;
+        const double fasy = w * fa * q[p];
+        outf[2 * p + 1] = fma(omw, f[2 * p + 1], fsym + fasy);
+        outf[2 * p + 2] = fma(omw, f[2 * p + 2], fsym - fasy);
+        const double gsym = w * fma(k2, q[p] * q[p], k1);
+        const double gasy = w * k3 * q[p];
+        outg[2 * p + 1] = fma(omw, gg[2 * p + 1], gsym + gasy);
+        outg[2 * p + 2] = fma(omw, gg[2 * p + 2], gsym - gasy);
+    }
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        B[i * S + idx] = outf[i];
+        B[(19 + i) * S + idx] = outg[i];
+    }
+    if (XBC != XBC_PERIODIC && x == g.nx - 2) {  // outflow ghost x = nx-1 copies x = nx-2
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            B[i * S + idx + 1] = outf[i];
+            B[(19 + i) * S + idx + 1] = outg[i];
+        }
+    }
+    if (XBC == XBC_OUTFLOW_BOTH && x == 1) {  // outflow ghost x = 0 copies x = 1
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            B[i * S + idx - 1] = outf[i];
+            B[(19 + i) * S + idx - 1] = outg[i];
+        }
+    }
+    if (count) count_flags(cnt, unphys, nonpos, (unsigned long long)step_index * (unsigned long long)g.N + idx);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 deviation step.  Populations are stored as d_i = p_i - p_i^ref with
+// p^ref the rest equilibrium of (n_ref, eps_ref): f_i^ref = w_i n_ref,
+// g_i^ref = w_i eps_ref / c_l^2 (i > 0), g_0^ref = w_0 eps_ref (3 - 2/c_l^2).
+// Streaming and BGK are linear and the reference is uniform and symmetric, so
+// the step maps deviations to deviations.  The moments are the reference
+// moments (n_ref, eps_ref, 0) plus the float sums of the deviations; the
+// recovery, where the strong-shock cancellation sits, runs in FP64:
+//   E = eps_ref + sum dg,  sqrt(E^2 - 3M^2/4) and 1/(3E + eps) each from a
+//   binary32 seed and one FP64 Newton correction (relative error ~1e-14),
+//   eps = 2 sqrt(...) - E, beta = 3 M / (3E + eps), 1 - |beta|^2 in FP64.
+// The equilibrium deviations are formed without cancellation:
+//   df_i = w_i [dS + 3 S q_i / c_l]
+//   dg_i = w_i [d_eps / c_l^2 + eps gamma^2 (6 q_i^2 - 2 b2) / c_l^2] +- w_i eps gamma^2 4 q_i / c_l
+//   dg_0 = w_0 [d_eps (3 - 2/c_l^2) + eps gamma^2 b2 (4 - 2/c_l^2)]
+// with dS = sum df, d_eps = eps - eps_ref (FP64, then rounded).
+// ---------------------------------------------------------------------------
+struct Dev32 {
+    float omega, omw, c_l, inv_cl, inv_cl2, n_ref;
+    float g0a, g0b;  // 3 - 2/c_l^2 and 4 - 2/c_l^2
+    double eps_ref;
+};
+
+template <int XBC, bool SOLID>
+__global__ void __launch_bounds__(256) k_step_f32(const float* __restrict__ A, float* __restrict__ B, Geom g,
+                                                  Dev32 c, Counters cnt, int count, long long step_index) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= g.N) return;
+    int x, y, z;
+    cell_coords(g, idx, x, y, z);
+    const long long S = g.S;
+    if (XBC != XBC_PERIODIC && (x == 0 || x == g.nx - 1)) {
+        if (XBC == XBC_INFLOW_OUTFLOW && x == 0) {
+#pragma unroll
+            for (int q = 0; q < 38; ++q) B[q * S + idx] = __ldg(A + q * S + idx);
+        }
+        return;
+    }
+    const PullOffsets o(g, x, y, z);
+    float f[19], gg[19];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const int s = idx + o.src(i);
+        f[i] = __ldg(A + i * S + s);
+        gg[i] = __ldg(A + (19 + i) * S + s);
+    }
+    if (SOLID) {
+        if (is_solid(f[0])) {
+            const float m = solid_marker_f();
+#pragma unroll
+            for (int q = 0; q < 38; ++q) B[q * S + idx] = m;
+            return;
+        }
+#pragma unroll
+        for (int i = 1; i < 19; ++i) {
+            if (is_solid(f[i])) {
+                f[i] = __ldg(A + opp(i) * S + idx);
+                gg[i] = __ldg(A + (19 + opp(i)) * S + idx);
+            }
+        }
+    }
+    float dS, dE, mxf, myf, mzf;
+    moments_pairs(f, gg, dS, dE, mxf, myf, mzf);
+    mxf *= c.c_l;
+    myf *= c.c_l;
+    mzf *= c.c_l;
+    // ---- FP64 recovery ----
+    const double E = c.eps_ref + (double)dE;
+    const double Mx = mxf, My = myf, Mz = mzf;
+    const double m2 = fma(Mx, Mx, fma(My, My, Mz * Mz));
+    const double d4 = fma(E, E, -0.75 * m2);  // (4E^2 - 3M^2)/4
+    const float y0 = rsqrtf((float)d4);
+    const double s0 = d4 * (double)y0;
+    const double sres = fma(-s0, s0, d4);
+    const double s = fma(sres, (double)(0.5f * y0), s0);  // sqrt(d4), one Newton step
+    const double eps = fma(2.0, s, -E);
+    const double D = fma(3.0, E, eps);
+    const double r0 = (double)(1.0f / (float)D);
+    const double rr = fma(r0, fma(-D, r0, 1.0), r0);  // 1/D, one Newton step
+    const double r3 = 3.0 * rr;
+    const double bx = Mx * r3, by = My * r3, bz = Mz * r3;
+    const double b2 = fma(bx, bx, fma(by, by, bz * bz));
+    const double omb2 = 1.0 - b2;
+    const bool unphys = !(pos_finite((double)c.n_ref + (double)dS) && pos_finite(E) && nonneg_finite(d4) &&
+                          pos_finite(eps) && below_one(b2));
+    const float deps = (float)(eps - c.eps_ref);
+    // ---- FP32 equilibria and BGK ----
+    const float bxf = (float)bx, byf = (float)by, bzf = (float)bz, b2f = (float)b2;
+    const bool nonpos = nonpositive_eq(bxf, byf, bzf, c.c_l);
+    const float gam2 = 1.0f / (float)omb2;
+    const float epsf = (float)eps;
+    const float eg = epsf * gam2;
+    const float sfull = c.n_ref + dS;
+    const float om = c.omega;
+    const float qv[9] = {bxf, byf, bzf, bxf + byf, bxf - byf, bxf + bzf, bxf - bzf, byf + bzf, byf - bzf};
+    const float fa = 3.0f * sfull * c.inv_cl;
+    const float k1 = (deps - 2.0f * eg * b2f) * c.inv_cl2;
+    const float k2 = 6.0f * eg * c.inv_cl2;
+    const float k3 = 4.0f * eg * c.inv_cl;
+    float outf[19], outg[19];
+    {
+        const float feq0 = (float)kW0 * dS;
+        outf[0] = fmaf(om, feq0 - f[0], f[0]);
+        const float geq0 = (float)kW0 * (deps * c.g0a + eg * b2f * c.g0b);
+        outg[0] = fmaf(om, geq0 - gg[0], gg[0]);
+    }
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        const float w = (float)pair_w(p);
+        const float fsym = w * dS;
+        const float fasy = w * fa * qv[p];
+        outf[2 * p + 1] = fmaf(om, (fsym + fasy) - f[2 * p + 1], f[2 * p + 1]);
+        outf[2 * p + 2] = fmaf(om, (fsym - fasy) - f[2 * p + 2], f[2 * p + 2]);
+        const float gsym = w * fmaf(k2, qv[p] * qv[p], k1);
+        const float gasy = w * k3 * qv[p];
+        outg[2 * p + 1] = fmaf(om, (gsym + gasy) - gg[2 * p + 1], gg[2 * p + 1]);
+        outg[2 * p + 2] = fmaf(om, (gsym - gasy) - gg[2 * p + 2], gg[2 * p + 2]);
+    }
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        B[i * S + idx] = outf[i];
+        B[(19 + i) * S + idx] = outg[i];
+    }
+    if (XBC != XBC_PERIODIC && x == g.nx - 2) {
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            B[i * S + idx + 1] = outf[i];
+            B[(19 + i) * S + idx + 1] = outg[i];
+        }
+    }
+    if (XBC == XBC_OUTFLOW_BOTH && x == 1) {
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            B[i * S + idx - 1] = outf[i];
+            B[(19 + i) * S + idx - 1] = outg[i];
+        }
+    }
+    if (count) count_flags(cnt, unphys, nonpos, (unsigned long long)step_index * (unsigned long long)g.N + idx);
+}
+
+// ---------------------------------------------------------------------------
+// Equilibria of given fields in FP64 (initialisation and inflow plane):
+// Eqs. (equil1s), (equil2as), (equil2bs).
+// ---------------------------------------------------------------------------
+__device__ void equilibrium_f64(double n, double eps, double bx, double by, double bz, const Phys& ph, double* f,
+                                double* g) {
+    const double b2 = bx * bx + by * by + bz * bz;
+    const double gam2 = 1.0 / (1.0 - b2);
+    const double ng = n * sqrt(gam2);
+    const double eg = eps * gam2;
+    const double q[9] = {bx, by, bz, bx + by, bx - by, bx + bz, bx - bz, by + bz, by - bz};
+    f[0] = kW0 * ng;
+    g[0] = kW0 * (4.0 * eg - eps * (2.0 * ph.inv_cl2 + 1.0) - 2.0 * eg * b2 * ph.inv_cl2);
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        const double w = pair_w(p);
+        const double fa = 3.0 * q[p] * ph.inv_cl;
+        f[2 * p + 1] = w * ng * (1.0 + fa);
+        f[2 * p + 2] = w * ng * (1.0 - fa);
+        const double gs = eps * ph.inv_cl2 + eg * (6.0 * q[p] * q[p] - 2.0 * b2) * ph.inv_cl2;
+        const double ga = eg * 4.0 * q[p] * ph.inv_cl;
+        g[2 * p + 1] = w * (gs + ga);
+        g[2 * p + 2] = w * (gs - ga);
+    }
+}
+
+// Rest equilibrium of the FP32 deviation reference.
+__device__ __forceinline__ void reference_eq(const Phys& ph, double* fr, double* gr) {
+    fr[0] = kW0 * ph.n_ref;
+    gr[0] = kW0 * ph.eps_ref * (3.0 - 2.0 * ph.inv_cl2);
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        const double w = pair_w(p);
+        fr[2 * p + 1] = fr[2 * p + 2] = w * ph.n_ref;
+        gr[2 * p + 1] = gr[2 * p + 2] = w * ph.eps_ref * ph.inv_cl2;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_init(const double* __restrict__ n, const double* __restrict__ eps,
+                                              const double* __restrict__ beta, const uint8_t* __restrict__ solid,
+                                              T* __restrict__ A, T* __restrict__ B, Geom g, Phys ph) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= g.N) return;
+    const long long S = g.S;
+    if (solid && solid[idx]) {
+        T m;
+        if constexpr (sizeof(T) == 8) m = solid_marker_d(); else m = solid_marker_f();
+        for (int q = 0; q < 38; ++q) A[q * S + idx] = B[q * S + idx] = m;
+        return;
+    }
+    const int x = idx % g.nx;
+    double f[19], gg[19];
+    if (g.xbc == XBC_INFLOW_OUTFLOW && x == 0)
+        equilibrium_f64(ph.n_in, ph.eps_in, ph.beta_in[0], ph.beta_in[1], ph.beta_in[2], ph, f, gg);
+    else
+        equilibrium_f64(n[idx], eps[idx], beta[idx], beta[g.N + idx], beta[2 * (long long)g.N + idx], ph, f, gg);
+    if constexpr (sizeof(T) == 4) {
+        double fr[19], gr[19];
+        reference_eq(ph, fr, gr);
+        for (int i = 0; i < 19; ++i) {
+            f[i] -= fr[i];
+            gg[i] -= gr[i];
+        }
+    }
+    for (int i = 0; i < 19; ++i) {
+        A[i * S + idx] = B[i * S + idx] = (T)f[i];
+        A[(19 + i) * S + idx] = B[(19 + i) * S + idx] = (T)gg[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Macroscopic output of a stored state (no gather: the moments of the
+// post-collision populations equal those of the gathered ones, the
+// collision conserves them).  IEEE sqrt and division.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(128) k_macro(const T* __restrict__ A, double* __restrict__ n,
+                                               double* __restrict__ eps, double* __restrict__ beta, Geom g,
+                                               Phys ph, unsigned long long* bad_count) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= g.N) return;
+    const long long S = g.S;
+    if (is_solid(A[idx])) {
+        const double nan = __longlong_as_double(0x7FF8000000000000ll);
+        n[idx] = eps[idx] = beta[idx] = beta[g.N + idx] = beta[2 * (long long)g.N + idx] = nan;
+        return;
+    }
+    double f[19], gg[19];
+    for (int i = 0; i < 19; ++i) {
+        f[i] = (double)A[i * S + idx];
+        gg[i] = (double)A[(19 + i) * S + idx];
+    }
+    double sf, E, mx, my, mz;
+    moments_pairs(f, gg, sf, E, mx, my, mz);
+    if constexpr (sizeof(T) == 4) {
+        sf += ph.n_ref;
+        E += ph.eps_ref;
+    }
+    mx *= ph.c_l;
+    my *= ph.c_l;
+    mz *= ph.c_l;
+    const double m2 = mx * mx + my * my + mz * mz;
+    const double disc = 4.0 * E * E - 3.0 * m2;
+    const double e = sqrt(disc) - E;
+    const double D = 3.0 * E + e;
+    const double bx = 3.0 * mx / D, by = 3.0 * my / D, bz = 3.0 * mz / D;
+    const double b2 = bx * bx + by * by + bz * bz;
+    const double nn = sf * sqrt(1.0 - b2);
+    n[idx] = nn;
+    eps[idx] = e;
+    beta[idx] = bx;
+    beta[g.N + idx] = by;
+    beta[2 * (long long)g.N + idx] = bz;
+    const bool bad = !(pos_finite(sf) && pos_finite(E) && nonneg_finite(disc) && pos_finite(e) && below_one(b2) &&
+                       pos_finite(nn));
+    if (bad) atomicAdd(bad_count, 1ull);
+}
+
+__global__ void k_check_solid_planes(Geom g, const uint8_t* __restrict__ solid, unsigned long long* flag) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int plane = g.ny * g.nz;
+    if (t >= 4 * plane) return;
+    const int which = t / plane, yz = t - which * plane;
+    const int xs[4] = {0, 1, g.nx - 2, g.nx - 1};
+    if (solid[(long long)yz * g.nx + xs[which]]) atomicAdd(flag, 1ull);
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+static inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+cudaError_t launch_init(int prec, const Geom& g, const Phys& ph, const double* n, const double* eps,
+                        const double* beta, const uint8_t* solid, void* A, void* B, cudaStream_t st) {
+    g_last_launches = 1;
+    if (prec == 0)
+        k_init<double><<<blocks_for(g.N, 128), 128, 0, st>>>(n, eps, beta, solid, (double*)A, (double*)B, g, ph);
+    else
+        k_init<float><<<blocks_for(g.N, 128), 128, 0, st>>>(n, eps, beta, solid, (float*)A, (float*)B, g, ph);
+    return cudaGetLastError();
+}
+
+template <int XBC, bool SOLID>
+static void launch_step_t(int prec, const Geom& g, const Phys& ph, const void* A, void* B, Counters cnt, bool count,
+                          long long step_index, cudaStream_t st) {
+    if (prec == 0) {
+        k_step_f64<XBC, SOLID><<<blocks_for(g.N, 128), 128, 0, st>>>((const double*)A, (double*)B, g, ph, cnt,
+                                                                      count ? 1 : 0, step_index);
+    } else {
+        Dev32 c;
+        c.omega = (float)ph.omega;
+        c.omw = (float)(1.0 - ph.omega);
+        c.c_l = (float)ph.c_l;
+        c.inv_cl = (float)ph.inv_cl;
+        c.inv_cl2 = (float)ph.inv_cl2;
+        c.n_ref = (float)ph.n_ref;
+        c.g0a = (float)(3.0 - 2.0 * ph.inv_cl2);
+        c.g0b = (float)(4.0 - 2.0 * ph.inv_cl2);
+        c.eps_ref = ph.eps_ref;
+        k_step_f32<XBC, SOLID><<<blocks_for(g.N, 256), 256, 0, st>>>((const float*)A, (float*)B, g, c, cnt,
+                                                                      count ? 1 : 0, step_index);
+    }
+}
+
+cudaError_t launch_step(int prec, const Geom& g, const Phys& ph, const void* A, void* B, Counters cnt, bool count,
+                        long long step_index, cudaStream_t st) {
+    // The solid-marker checks are always compiled in: a lattice without
+    // solid cells never matches the marker, and the check costs no memory
+    // traffic.
+    g_last_launches = 1;
+    switch (g.xbc) {
+        case XBC_PERIODIC: launch_step_t<XBC_PERIODIC, true>(prec, g, ph, A, B, cnt, count, step_index, st); break;
+        case XBC_INFLOW_OUTFLOW:
+            launch_step_t<XBC_INFLOW_OUTFLOW, true>(prec, g, ph, A, B, cnt, count, step_index, st);
+            break;
+        default: launch_step_t<XBC_OUTFLOW_BOTH, true>(prec, g, ph, A, B, cnt, count, step_index, st); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_macro(int prec, const Geom& g, const Phys& ph, const void* A, double* n, double* eps,
+                         double* beta, Counters cnt, cudaStream_t st) {
+    g_last_launches = 1;
+    if (prec == 0)
+        k_macro<double><<<blocks_for(g.N, 128), 128, 0, st>>>((const double*)A, n, eps, beta, g, ph, cnt.macro_bad);
+    else
+        k_macro<float><<<blocks_for(g.N, 128), 128, 0, st>>>((const float*)A, n, eps, beta, g, ph, cnt.macro_bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_solid_planes(const Geom& g, const uint8_t* solid, unsigned long long* flag,
+                                      cudaStream_t st) {
+    g_last_launches = 1;
+    const long long n = 4ll * g.ny * g.nz;
+    k_check_solid_planes<<<blocks_for(n, 256), 256, 0, st>>>(g, solid, flag);
+    return cudaGetLastError();
+}
+
+}  // namespace rlb

@@ -1,0 +1,68 @@
+// rlb_internal.h -- types shared by the host API and the kernels of librlb.
+//
+// Kernel argument blocks and the launcher functions that each .cu file
+// exports to the C-ABI layer (rlb_api.cu).  Nothing here is part of the
+// public ABI (include/rlb.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rlb {
+
+enum : int { XBC_PERIODIC = 0, XBC_INFLOW_OUTFLOW = 1, XBC_OUTFLOW_BOTH = 2 };
+
+// Number of counter slots that warps spread their statistics over.
+constexpr int kCounterSlots = 4096;
+
+// Lattice geometry.  Populations of plane q (0..37) of a state start at
+// element q * S; cell index c = (z*ny + y)*nx + x.
+struct Geom {
+    int nx, ny, nz;
+    int nxy;     // nx * ny
+    int N;       // nx * ny * nz (< 2^31)
+    long long S; // plane stride in elements (N rounded up to a multiple of 64)
+    int xbc;
+};
+
+// Physical parameters, with the derived constants the kernels use.
+struct Phys {
+    double tau, omega, c_l;
+    double inv_cl, inv_cl2;
+    double n_in, eps_in, beta_in[3];
+    double n_ref, eps_ref;  // FP32 deviation reference (beta = 0)
+};
+
+// Device-side statistics of a run (see rlb_stats).
+struct Counters {
+    unsigned long long* slots;      // [2][kCounterSlots]: unphysical, non-positive equilibria
+    unsigned long long* first_bad;  // min over flagged updates of step*N + cell
+    unsigned long long* macro_bad;  // cells flagged by the last macro evaluation
+};
+
+// Launchers (return the launch error, enqueue on 'stream').
+cudaError_t launch_init(int prec, const Geom& g, const Phys& ph, const double* n, const double* eps,
+                        const double* beta, const uint8_t* solid, void* A, void* B, cudaStream_t stream);
+cudaError_t launch_step(int prec, const Geom& g, const Phys& ph, const void* A, void* B, Counters cnt,
+                        bool count, long long step_index, cudaStream_t stream);
+cudaError_t launch_macro(int prec, const Geom& g, const Phys& ph, const void* A, double* n, double* eps,
+                         double* beta, Counters cnt, cudaStream_t stream);
+cudaError_t launch_check_solid_planes(const Geom& g, const uint8_t* solid, unsigned long long* flag,
+                                      cudaStream_t stream);
+
+// Adjoint.  'red' holds kAdjBlocksMax * 4 doubles of per-block partial sums.
+constexpr int kAdjBlocksMax = 152 * 16;
+cudaError_t launch_adjoint_macro(int prec, const Geom& g, const Phys& ph, const void* A, const double* dn,
+                                 const double* deps, const double* dbeta, void* lam, cudaStream_t stream);
+cudaError_t launch_adjoint_step(int prec, const Geom& g, const Phys& ph, const void* A, const void* lam_in,
+                                void* lam_out, double* red, double* dtau, double* dbeta_in, cudaStream_t stream);
+cudaError_t launch_adjoint_fields(int prec, const Geom& g, const Phys& ph, const double* n0, const double* eps0,
+                                  const double* beta0, const void* A0, const void* lam0, double* dn0,
+                                  double* deps0, double* dbeta0, double* red, double* dbeta_in,
+                                  cudaStream_t stream);
+
+// Kernel launches issued by the last launcher call (for accounting).
+int last_launch_count();
+void set_last_launch_count(int n);
+
+}  // namespace rlb

@@ -1,0 +1,158 @@
+"""Python front end of librlb: one relativistic lattice Boltzmann lattice on one GPU.
+
+``RLB`` owns a librlb context whose device workspace is a torch tensor (the
+caching allocator provides the memory, torch's current stream orders the
+work).  Every method marshals arguments to the C entry point of the same name
+in ``_native``; the computation runs in the library's CUDA kernels only.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+_PREC = {"fp64": N.RLB_FP64, "fp32": N.RLB_FP32_DEV, "fp32dev": N.RLB_FP32_DEV}
+_XBC = {"periodic": N.RLB_BC_PERIODIC, "inflow_outflow": N.RLB_BC_INFLOW_OUTFLOW,
+        "outflow_both": N.RLB_BC_OUTFLOW_BOTH}
+
+
+def _require_cuda(device):
+    if not torch.cuda.is_available():
+        raise RuntimeError("librlb needs a CUDA GPU; there is no CPU path")
+    return torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+
+
+class RLB:
+    """A D3Q19 relativistic lattice Boltzmann lattice (f and g populations) on one GPU."""
+
+    def __init__(self, nx, ny, nz, tau, c_l=1.0, precision="fp64", xbc="periodic", n_in=1.0, eps_in=1.0,
+                 beta_in=(0.0, 0.0, 0.0), n_ref=1.0, eps_ref=1.0, device=None, stream=None):
+        self.device = _require_cuda(device)
+        prec = _PREC[precision] if isinstance(precision, str) else int(precision)
+        x = _XBC[xbc] if isinstance(xbc, str) else int(xbc)
+        self.params = N.make_params(nx, ny, nz, tau, c_l, prec, x, n_in, eps_in, beta_in, n_ref, eps_ref)
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.N = self.nx * self.ny * self.nz
+        self.precision = "fp64" if prec == N.RLB_FP64 else "fp32"
+        self.dtype = torch.float64 if prec == N.RLB_FP64 else torch.float32
+        self.plane_stride, self.elem_bytes, self.state_bytes = N.rlb_state_layout(self.params)
+        self.ws_bytes = N.rlb_workspace_bytes(self.params)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+            self.ctx = N.rlb_create(self.params, self.stream.cuda_stream, self.ws, self.ws_bytes)
+
+    @classmethod
+    def from_workload(cls, w, precision="fp64", device=None, n_ref=None, eps_ref=None, **kw):
+        """Context for a ``workloads.Workload``; the FP32 reference defaults to the
+        volume means of the initial fields over non-solid cells."""
+        if n_ref is None or eps_ref is None:
+            m = np.ones(w.eps.shape, bool) if w.solid is None else (w.solid == 0)
+            n_ref = float(np.mean(w.n[m])) if n_ref is None else n_ref
+            eps_ref = float(np.mean(w.eps[m])) if eps_ref is None else eps_ref
+        xbc = {0: "periodic", 1: "inflow_outflow", 2: "outflow_both"}[w.xbc]
+        return cls(w.nx, w.ny, w.nz, w.tau, w.c_l, precision, xbc, w.n_in, w.eps_in, w.beta_in, n_ref, eps_ref,
+                   device=device, **kw)
+
+    # -- memory ---------------------------------------------------------------
+    def new_state(self) -> torch.Tensor:
+        """A state-layout device buffer (38 planes of plane_stride elements)."""
+        return torch.empty((38, self.plane_stride), dtype=self.dtype, device=self.device)
+
+    def _view(self, ptr: int) -> torch.Tensor:
+        off = ptr - self.ws.data_ptr()
+        assert 0 <= off and off + self.state_bytes <= self.ws_bytes
+        return self.ws[off:off + self.state_bytes].view(self.dtype).view(38, self.plane_stride)
+
+    def state(self) -> torch.Tensor:
+        """View of the context's current state (valid until the next step)."""
+        return self._view(N.rlb_state_ptr(self.ctx))
+
+    # -- forward --------------------------------------------------------------
+    def init_fields(self, n, eps, beta, solid=None):
+        """Initial fields as torch tensors on the device (float64; solid uint8)
+        or numpy arrays on the host; n, eps (nz, ny, nx), beta (3, nz, ny, nx)."""
+        if isinstance(n, torch.Tensor):
+            args = [t.contiguous() for t in (n, eps, beta)]
+            for t in args:
+                assert t.dtype == torch.float64 and t.device == self.device and t.numel() in (self.N, 3 * self.N)
+            s = None if solid is None else solid.to(self.device, torch.uint8).contiguous()
+            with torch.cuda.device(self.device):
+                N.rlb_init_fields(self.ctx, *args, s, N.RLB_DEVICE)
+            self._keep = (args, s)
+        else:
+            args = [np.ascontiguousarray(a, dtype=np.float64) for a in (n, eps, beta)]
+            s = None if solid is None else np.ascontiguousarray(solid, dtype=np.uint8)
+            with torch.cuda.device(self.device):
+                N.rlb_init_fields(self.ctx, *args, s, N.RLB_HOST)
+        return self
+
+    def step(self, nsteps: int = 1):
+        N.rlb_step(self.ctx, nsteps)
+        return self
+
+    def step_into(self, src: torch.Tensor, dst: torch.Tensor):
+        N.rlb_step_into(self.ctx, src, dst)
+
+    def save_state(self, dst: torch.Tensor):
+        N.rlb_save_state(self.ctx, dst)
+
+    def load_state(self, src: torch.Tensor):
+        N.rlb_load_state(self.ctx, src)
+
+    def macro(self, state: torch.Tensor | None = None, where: str = "device"):
+        """(n, eps, beta, ok): n, eps (nz, ny, nx), beta (3, nz, ny, nx); NaN at solid cells;
+        ok is False when some cell failed the recovery (outputs are still written)."""
+        shp = (self.nz, self.ny, self.nx)
+        if where == "device":
+            n = torch.empty(shp, dtype=torch.float64, device=self.device)
+            e = torch.empty(shp, dtype=torch.float64, device=self.device)
+            b = torch.empty((3,) + shp, dtype=torch.float64, device=self.device)
+            st = N.rlb_macro(self.ctx, state, n, e, b, N.RLB_DEVICE)
+        else:
+            n, e, b = np.empty(shp), np.empty(shp), np.empty((3,) + shp)
+            st = N.rlb_macro(self.ctx, state, n, e, b, N.RLB_HOST)
+        return n, e, b, st == N.RLB_OK
+
+    def stats(self) -> dict:
+        return N.rlb_stats(self.ctx)
+
+    def sync(self):
+        N.rlb_sync(self.ctx)
+
+    @property
+    def launches(self) -> int:
+        return N.rlb_launch_count(self.ctx)
+
+    # -- adjoint --------------------------------------------------------------
+    def adjoint_macro(self, state, dL_dn, dL_deps, dL_dbeta, lam_out):
+        N.rlb_adjoint_macro(self.ctx, state, dL_dn.contiguous(), dL_deps.contiguous(), dL_dbeta.contiguous(), lam_out)
+
+    def adjoint_step(self, state_t, lam_in, lam_out, dtau_acc, dbeta_in_acc):
+        N.rlb_adjoint_step(self.ctx, state_t, lam_in, lam_out, dtau_acc, dbeta_in_acc)
+
+    def adjoint_fields(self, n0, eps0, beta0, lam0, dn0, deps0, dbeta0, dbeta_in_acc):
+        N.rlb_adjoint_fields(self.ctx, n0, eps0, beta0, lam0, dn0, deps0, dbeta0, dbeta_in_acc)
+
+    # -- lifetime -------------------------------------------------------------
+    def close(self):
+        if getattr(self, "ctx", None):
+            N.rlb_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- layout helpers (marshalling between the state layout and arrays) -----
+    def state_to_cells(self, state: torch.Tensor) -> torch.Tensor:
+        """(38, plane_stride) -> (nz, ny, nx, 2, 19) (cell-major, f then g)."""
+        return state[:, :self.N].T.reshape(self.nz, self.ny, self.nx, 2, 19)
+
+    def cells_to_state(self, cells: torch.Tensor) -> torch.Tensor:
+        out = torch.zeros((38, self.plane_stride), dtype=self.dtype, device=self.device)
+        out[:, :self.N] = cells.reshape(self.N, 38).T.to(self.dtype)
+        return out

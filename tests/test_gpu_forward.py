@@ -1,0 +1,228 @@
+"""Parity of the CUDA forward path (through the C ABI) with the FP64 oracle.
+
+FP64 path: max relative error of n, eps, beta <= 1e-10; FP32 deviation path:
+<= 1e-4, after the stated step counts.  Population-level comparisons on tiny
+grids, statistics counters compared exactly.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+from tests._helpers import gpu_run, oracle_run, rel_errors, tiny_workload
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "fp32": 1e-4}
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+TINY = [
+    dict(nx=1, ny=1, nz=1, xbc=0, solid=()),
+    dict(nx=2, ny=3, nz=4, xbc=0, solid=()),
+    dict(nx=3, ny=3, nz=3, xbc=0, solid=((1, 1, 1),)),
+    dict(nx=5, ny=4, nz=3, xbc=0, solid=((2, 1, 1), (3, 1, 1))),
+    dict(nx=7, ny=5, nz=3, xbc=1, solid=((3, 2, 1),)),
+    dict(nx=3, ny=2, nz=2, xbc=1, solid=()),
+    dict(nx=9, ny=1, nz=1, xbc=2, solid=()),
+    dict(nx=37, ny=11, nz=5, xbc=0, solid=((10, 5, 2), (11, 5, 2), (10, 6, 2))),  # spans blocks, ragged tail
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", TINY, ids=[f"{c['nx']}x{c['ny']}x{c['nz']}_bc{c['xbc']}" for c in TINY])
+def test_tiny_grids_populations_and_stats(case, prec):
+    w = tiny_workload(case["nx"], case["ny"], case["nz"], case["xbc"], seed=7, solid_cells=case["solid"])
+    steps = 12
+    stats = oracle.Stats()
+    ref, st_ref = oracle_run(w, steps, stats)
+    got, sim = gpu_run(w, steps, prec)
+    en, ee, eb = rel_errors(got, ref, w.solid)
+    assert max(en, ee, eb) <= TOL[prec], (en, ee, eb)
+    s = sim.stats()
+    assert s["steps"] == steps
+    assert s["n_unphysical"] == stats.n_unphysical == 0
+    assert s["n_nonpositive_eq"] == stats.n_nonpositive_eq
+    if prec == "fp64":
+        # population-level parity (oracle layout is cell-major)
+        cells = sim.state_to_cells(sim.state()).cpu().numpy()
+        fluid = np.ones(cells.shape[:3], bool) if w.solid is None else w.solid == 0
+        d = np.abs(cells - st_ref)[fluid]
+        assert np.max(d / np.maximum(np.abs(st_ref[fluid]), 1e-300)) < 1e-11
+        if w.solid is not None:
+            marker = cells[w.solid == 1]
+            assert np.all(np.isnan(marker))
+    sim.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_shock_tube_1600_2000_steps(prec):
+    """The 1D shock tube: 1600 x 1 x 1, tau 0.9, 2000 steps, outflow ghosts."""
+    w = W.shock_tube_1d()
+    stats = oracle.Stats()
+    ref, _ = oracle_run(w, w.steps, stats)
+    got, sim = gpu_run(w, w.steps, prec)
+    en, ee, eb = rel_errors(got, ref)
+    assert max(en, ee, eb) <= TOL[prec], (en, ee, eb)
+    s = sim.stats()
+    assert s["n_unphysical"] == stats.n_unphysical
+    if prec == "fp64":
+        assert s["n_nonpositive_eq"] == stats.n_nonpositive_eq
+    else:  # binary32 populations shift beta in the last bits; the count may differ near the bound
+        assert abs(s["n_nonpositive_eq"] - stats.n_nonpositive_eq) <= 1e-4 * stats.n_nonpositive_eq
+    sim.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_sphere_reduced_500_steps(prec):
+    """The sphere workload at 60 x 30 x 30 (sphere scaled with the box), 500 steps."""
+    w = W.sphere_3d(nx=60, ny=30, nz=30)
+    ref, _ = oracle_run(w, 500)
+    got, sim = gpu_run(w, 500, prec)
+    en, ee, eb = rel_errors(got, ref, w.solid)
+    assert max(en, ee, eb) <= TOL[prec], (en, ee, eb)
+    sim.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_sphere_full_size_short(prec):
+    """Full 200 x 100 x 100 sphere lattice, 10 steps, every cell compared."""
+    w = W.sphere_3d()
+    stats = oracle.Stats()
+    ref, _ = oracle_run(w, 10, stats)
+    got, sim = gpu_run(w, 10, prec)
+    en, ee, eb = rel_errors(got, ref, w.solid)
+    assert max(en, ee, eb) <= TOL[prec], (en, ee, eb)
+    s = sim.stats()
+    if prec == "fp64":
+        assert s["n_nonpositive_eq"] == stats.n_nonpositive_eq
+    sim.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_sphere_full_size_5000_steps_sampled(prec):
+    """Full-size sphere run to 5000 steps against the stored oracle samples."""
+    path = os.path.join(GOLDEN, "sphere_fp64_5000.json")
+    if not os.path.exists(path):
+        pytest.skip("sampled oracle reference not generated")
+    with open(path) as fh:
+        g = json.load(fh)
+    w = W.sphere_3d(steps=g["steps"])
+    got, sim = gpu_run(w, g["steps"], prec)
+    cells = np.array(g["cells"])
+    n = got[0].reshape(-1)[cells]
+    e = got[1].reshape(-1)[cells]
+    b = np.stack([got[2][a].reshape(-1)[cells] for a in range(3)])
+    ref = (np.array(g["n"]), np.array(g["eps"]), np.array(g["beta"]))
+    en, ee, eb = rel_errors((n, e, b), ref)
+    assert max(en, ee, eb) <= TOL[prec], (en, ee, eb)
+    s = sim.stats()
+    assert s["n_unphysical"] == g["stats"]["n_unphysical"]
+    sim.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_random_box_64(prec):
+    """Periodic box with the Gaussian-random-field recipe (sigma = 8) at 64^3, 200 steps."""
+    w = W.random_box(L=64, steps=200)
+    ref, _ = oracle_run(w, 200)
+    got, sim = gpu_run(w, 200, prec)
+    en, ee, eb = rel_errors(got, ref)
+    assert max(en, ee, eb) <= TOL[prec], (en, ee, eb)
+    sim.close()
+
+
+def test_tachyon_lattice_speed():
+    """c_l = 10 (numerical tachyons) with beta up to 0.6 in a periodic box."""
+    w = tiny_workload(16, 8, 6, 0, seed=3, c_l=10.0, bmax=0.6)
+    for prec in ("fp64", "fp32"):
+        stats = oracle.Stats()
+        ref, _ = oracle_run(w, 50, stats)
+        got, sim = gpu_run(w, 50, prec)
+        en, ee, eb = rel_errors(got, ref)
+        assert max(en, ee, eb) <= TOL[prec], (prec, en, ee, eb)
+        sim.close()
+
+
+def test_step_into_matches_step():
+    w = tiny_workload(12, 6, 5, 1, seed=5, solid_cells=((5, 3, 2),))
+    from paper_0912_2913_gb300 import RLB
+
+    sim = RLB.from_workload(w, "fp64", device="cuda:0").init_fields(w.n, w.eps, w.beta, w.solid)
+    a = sim.state().clone()
+    b = torch.full_like(a, float("nan"))
+    sim.step_into(a, b)
+    sim.step(1)
+    torch.cuda.synchronize()
+    assert torch.equal(sim.state()[:, :sim.N], b[:, :sim.N])
+    sim.close()
+
+
+def test_device_and_host_init_agree():
+    w = W.sphere_3d(nx=30, ny=16, nz=14)
+    from paper_0912_2913_gb300 import RLB
+
+    s1 = RLB.from_workload(w, "fp32", device="cuda:0").init_fields(w.n, w.eps, w.beta, w.solid)
+    dev = lambda a, dt=torch.float64: torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0", dt)
+    s2 = RLB.from_workload(w, "fp32", device="cuda:0").init_fields(dev(w.n), dev(w.eps), dev(w.beta),
+                                                                   dev(w.solid, torch.uint8))
+    torch.cuda.synchronize()
+    x1, x2 = s1.state()[:, :s1.N], s2.state()[:, :s2.N]
+    assert torch.equal(x1.isnan(), x2.isnan())
+    assert torch.equal(torch.nan_to_num(x1), torch.nan_to_num(x2))
+    s1.close()
+    s2.close()
+
+
+def test_errors_are_status_codes():
+    from paper_0912_2913_gb300 import RLB, RLBError
+    from paper_0912_2913_gb300 import _native as N
+
+    w = W.sphere_3d(nx=30, ny=16, nz=14)
+    bad = w.solid.copy()
+    bad[7, 8, 1] = 1  # solid next to the inflow ghost plane
+    sim = RLB.from_workload(w, "fp64", device="cuda:0")
+    with pytest.raises(RLBError) as ei:
+        sim.init_fields(w.n, w.eps, w.beta, bad)
+    assert ei.value.status == N.RLB_ERR_ARG
+    with pytest.raises(RLBError) as ei:
+        N.rlb_step(sim.ctx, 1)  # not initialised
+    assert ei.value.status == N.RLB_ERR_STATE
+    dev_bad = torch.from_numpy(bad).to("cuda:0")
+    with pytest.raises(RLBError):
+        sim.init_fields(*(torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (w.n, w.eps, w.beta)), dev_bad)
+    sim.init_fields(w.n, w.eps, w.beta, w.solid).step(2)
+    assert sim.stats()["steps"] == 2
+    sim.close()
+
+
+def test_unphysical_cells_are_counted_not_fatal():
+    """A state with T^00 < 0 somewhere: the run continues, the cells are
+    counted and rlb_macro reports RLB_ERR_UNPHYSICAL."""
+    w = tiny_workload(6, 4, 3, 0, seed=9)
+    from paper_0912_2913_gb300 import RLB
+
+    sim = RLB.from_workload(w, "fp64", device="cuda:0").init_fields(w.n, w.eps, w.beta)
+    st = sim.state()
+    st[19 + 0, 5] = -50.0  # T^00 < 0 in one cell
+    sim.step(1)
+    n, e, b, ok = sim.macro()
+    s = sim.stats()
+    assert s["n_unphysical"] >= 1 and s["first_bad"] >= 0
+    assert not ok
+    p = oracle.Params(**w.params())
+    ref = oracle.init(p, w.n, w.eps, w.beta)
+    ref.reshape(-1, 38)[5, 19 + 0] = -50.0
+    os_ = oracle.Stats()
+    oracle.run(p, ref, 1, stats=os_)
+    assert s["n_unphysical"] == os_.n_unphysical and s["first_bad"] == os_.first_bad
+    sim.close()

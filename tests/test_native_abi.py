@@ -1,0 +1,77 @@
+"""CPU checks of the C ABI library: it builds, loads, exports every symbol
+include/rlb.h declares, and validates parameters (no compute calls)."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def native():
+    from paper_0912_2913_gb300 import _native as N
+    from paper_0912_2913_gb300 import build
+
+    build.build()
+    N.load()
+    return N
+
+
+def declared_symbols():
+    with open(os.path.join(ROOT, "include", "rlb.h")) as fh:
+        text = fh.read()
+    return sorted(set(re.findall(r"RLB_API\s+[\w\s\*]+?\b(rlb_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_binding_exports():
+    from paper_0912_2913_gb300 import _native as N
+
+    assert declared_symbols() == sorted(N.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(native):
+    L = native.load()
+    for name in declared_symbols():
+        assert hasattr(L, name), name
+
+
+def test_parameter_validation(native):
+    N = native
+    ok = N.make_params(16, 8, 4, 0.8)
+    S, elem, nbytes = N.rlb_state_layout(ok)
+    assert S % 64 == 0 and S >= 16 * 8 * 4 and elem == 8 and nbytes == 38 * S * 8
+    p32 = N.make_params(200, 100, 100, 0.8, prec=N.RLB_FP32_DEV, xbc=N.RLB_BC_INFLOW_OUTFLOW, n_ref=0.3, eps_ref=0.1)
+    S, elem, nbytes = N.rlb_state_layout(p32)
+    assert elem == 4 and nbytes == 38 * S * 4
+    assert N.rlb_workspace_bytes(p32) >= 2 * nbytes
+    bad = [
+        N.make_params(0, 1, 1, 0.8),
+        N.make_params(4, 4, 4, 0.5),  # tau must be > 1/2
+        N.make_params(4, 4, 4, 0.8, c_l=0.0),
+        N.make_params(2, 4, 4, 0.8, xbc=N.RLB_BC_OUTFLOW_BOTH),  # ghost planes need nx >= 3
+        N.make_params(4, 4, 4, 0.8, xbc=N.RLB_BC_INFLOW_OUTFLOW, beta_in=(1.0, 0.0, 0.0)),
+        N.make_params(4, 4, 4, 0.8, prec=N.RLB_FP32_DEV, n_ref=0.0),
+        N.make_params(2048, 2048, 1024, 0.8),  # N >= 2^31
+    ]
+    for p in bad:
+        with pytest.raises(N.RLBError) as ei:
+            N.rlb_state_layout(p)
+        assert ei.value.status == N.RLB_ERR_ARG
+    p = N.make_params(4, 4, 4, 0.8)
+    p.reserved = 1
+    with pytest.raises(N.RLBError):
+        N.rlb_workspace_bytes(p)
+    assert N.rlb_status_str(N.RLB_ERR_UNPHYSICAL) == "RLB_ERR_UNPHYSICAL"
+
+
+def test_product_does_not_import_the_oracle():
+    """The product package never imports the oracle (test infrastructure)."""
+    pkg = os.path.join(ROOT, "paper_0912_2913_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                with open(os.path.join(dirpath, f)) as fh:
+                    src = fh.read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", src, re.M), f
+                assert "rlb_oracle" not in src, f
