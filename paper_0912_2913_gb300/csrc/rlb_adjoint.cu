@@ -160,7 +160,7 @@ __global__ void k_finalize(const double* __restrict__ red, int nblocks, double* 
 
 // Adjoint of eq(n, eps, beta) with respect to the fields (f with n gamma,
 // gamma = (1 - b2)^-1/2, d gamma / d beta = gamma^3 beta).
-__device__ void eq_fields_adjoint(const double* muf, const double* mug, double n, double eps, double bx, double by,
+__device__ __noinline__ void eq_fields_adjoint(const double* muf, const double* mug, double n, double eps, double bx, double by,
                                   double bz, const Phys& ph, double& an, double& ae, double& abx, double& aby,
                                   double& abz) {
     const double b2 = bx * bx + by * by + bz * bz;
@@ -179,15 +179,24 @@ __device__ void eq_fields_adjoint(const double* muf, const double* mug, double n
 }
 
 // ---------------------------------------------------------------------------
-// Step adjoint (T = double: FP64 states; T = float: FP32 deviation states,
-// recovery in FP64, adjoint arithmetic in FP32).
+// Step adjoint.  T = double: FP64 states and arithmetic.  T = float: FP32
+// deviation states; the recovery root runs in FP64 as in the forward FP32
+// kernel, everything else (equilibria, their adjoints, the recovery adjoint)
+// in binary32.  Two phases per cell (g, then f) keep the register footprint
+// near 60 values.
 // ---------------------------------------------------------------------------
+template <typename T>
+struct AdjConst {
+    T om, omw, c_l, inv_cl, inv_cl2, n_ref, g0a, g0b;
+    double eps_ref, inv_tau2;
+};
+
 template <typename T, int XBC>
-__global__ void __launch_bounds__(128) k_adjoint_step(const T* __restrict__ A, const T* __restrict__ Lin,
-                                                      T* __restrict__ Lout, Geom g, Phys ph, double* red) {
+__global__ void __launch_bounds__(128, (sizeof(T) == 4 ? 4 : 2))
+    k_adjoint_step(const T* __restrict__ A, const T* __restrict__ Lin, T* __restrict__ Lout, Geom g, Phys ph,
+                   AdjConst<T> c, double* red) {
     const long long S = g.S;
     double tau_acc = 0.0, bin0 = 0.0, bin1 = 0.0, bin2 = 0.0;
-    const double inv_tau2 = ph.omega * ph.omega;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < g.N; idx += gridDim.x * blockDim.x) {
         int x, y, z;
         cell_coords(g, idx, x, y, z);
@@ -219,143 +228,143 @@ __global__ void __launch_bounds__(128) k_adjoint_step(const T* __restrict__ A, c
             }
             continue;
         }
-        if (is_solid(A[idx])) {  // never updated: identity
+        if (is_solid(A[19 * S + idx])) {  // never updated: identity
 #pragma unroll
             for (int q = 0; q < 38; ++q) Lout[q * S + idx] = Lin[q * S + idx];
             continue;
         }
         const PullOffsets o(g, x, y, z);
-        T h[38];
-        bool bounced[19];
+        // mu = lambda_{t+1}(x), plus the outflow ghost that copies x
+        const int dup = (XBC != XBC_PERIODIC && x == g.nx - 2) ? 1 : ((XBC == XBC_OUTFLOW_BOTH && x == 1) ? -1 : 0);
+        auto load_mu = [&](int q) {
+            T v = Lin[q * S + idx];
+            if (dup) v += Lin[q * S + idx + dup];
+            return v;
+        };
+        // ---- phase 1: g -- gather, moments, recovery, g part of dL/dtau and of the adjoint
+        unsigned bounced = 0u;
+        T h[19];
 #pragma unroll
-        for (int i = 0; i < 19; ++i) {
-            const int s = idx + o.src(i);
-            h[i] = A[i * S + s];
-            h[19 + i] = A[(19 + i) * S + s];
-            bounced[i] = false;
-        }
+        for (int i = 0; i < 19; ++i) h[i] = A[(19 + i) * S + idx + o.src(i)];
 #pragma unroll
         for (int i = 1; i < 19; ++i) {
             if (is_solid(h[i])) {
-                bounced[i] = true;
-                h[i] = A[opp(i) * S + idx];
-                h[19 + i] = A[(19 + opp(i)) * S + idx];
+                bounced |= 1u << i;
+                h[i] = A[(19 + opp(i)) * S + idx];
             }
         }
-        T mu[38];
+        T dE = h[0], dd[9];
 #pragma unroll
-        for (int q = 0; q < 38; ++q) mu[q] = Lin[q * S + idx];
-        if (XBC != XBC_PERIODIC && x == g.nx - 2) {
-#pragma unroll
-            for (int q = 0; q < 38; ++q) mu[q] += Lin[q * S + idx + 1];
+        for (int p = 0; p < 9; ++p) {
+            dE += h[2 * p + 1] + h[2 * p + 2];
+            dd[p] = h[2 * p + 1] - h[2 * p + 2];
         }
-        if (XBC == XBC_OUTFLOW_BOTH && x == 1) {
-#pragma unroll
-            for (int q = 0; q < 38; ++q) mu[q] += Lin[q * S + idx - 1];
+        const T mx = c.c_l * (dd[0] + dd[3] + dd[4] + dd[5] + dd[6]);
+        const T my = c.c_l * (dd[1] + dd[3] - dd[4] + dd[7] + dd[8]);
+        const T mz = c.c_l * (dd[2] + dd[5] - dd[6] + dd[7] - dd[8]);
+        T Et, sqt, Dt, epst, e0, bx, by, bz, b2, gam2;
+        if constexpr (sizeof(T) == 8) {
+            const double E = dE;
+            const double sq = sqrt(4.0 * E * E - 3.0 * (mx * mx + my * my + mz * mz));
+            const double eps = sq - E;
+            const double D = 3.0 * E + eps;
+            const double r3 = 3.0 / D;
+            bx = mx * r3;
+            by = my * r3;
+            bz = mz * r3;
+            b2 = bx * bx + by * by + bz * bz;
+            gam2 = 1.0 / (1.0 - b2);
+            Et = E;
+            sqt = sq;
+            Dt = D;
+            epst = eps;
+            e0 = eps;
+        } else {
+            const double E = c.eps_ref + (double)dE;
+            const double Mx = mx, My = my, Mz = mz;
+            const double d4 = fma(E, E, -0.75 * fma(Mx, Mx, fma(My, My, Mz * Mz)));
+            const float y0 = rsqrtf((float)d4);
+            const double s0 = d4 * (double)y0;
+            const double s = fma(fma(-s0, s0, d4), (double)(0.5f * y0), s0);
+            const double eps = fma(2.0, s, -E);
+            Dt = (float)fma(3.0, E, eps);
+            e0 = (float)(eps - c.eps_ref);
+            epst = (float)eps;
+            Et = (float)E;
+            sqt = (float)(2.0 * s);
+            const float r3 = 3.0f / Dt;
+            bx = mx * r3;
+            by = my * r3;
+            bz = mz * r3;
+            b2 = fmaf(bx, bx, fmaf(by, by, bz * bz));
+            gam2 = 1.0f / (1.0f - b2);
         }
-        // ---- forward recompute: moments and recovery in FP64 ----
-        T sfT, ET, mxT, myT, mzT;
+        const T q[9] = {bx, by, bz, bx + by, bx - by, bx + bz, bx - bz, by + bz, by - bz};
+        const T eg = epst * gam2;
+        T mug[19];
+#pragma unroll
+        for (int i = 0; i < 19; ++i) mug[i] = load_mu(19 + i);
+        T tacc;
         {
-            T d[9];
-            T s = h[0];
-#pragma unroll
-            for (int i = 1; i < 19; ++i) s += h[i];
-            T es = h[19];
+            // g^eq (as stored: values for FP64, deviations for FP32)
+            const T geq0 = (sizeof(T) == 8) ? (T)kW0 * (4 * eg - epst * (2 * c.inv_cl2 + 1) - 2 * eg * b2 * c.inv_cl2)
+                                            : (T)kW0 * (e0 * c.g0a + eg * b2 * c.g0b);
+            tacc = mug[0] * (h[0] - geq0);
+            const T k1 = (e0 - 2 * eg * b2) * c.inv_cl2, k2 = 6 * eg * c.inv_cl2, k3 = 4 * eg * c.inv_cl;
 #pragma unroll
             for (int p = 0; p < 9; ++p) {
-                es += h[20 + 2 * p] + h[21 + 2 * p];
-                d[p] = h[20 + 2 * p] - h[21 + 2 * p];
+                const T w = (T)pair_w(p);
+                const T gs = w * (k2 * q[p] * q[p] + k1), ga = w * k3 * q[p];
+                tacc += mug[2 * p + 1] * (h[2 * p + 1] - (gs + ga)) + mug[2 * p + 2] * (h[2 * p + 2] - (gs - ga));
             }
-            sfT = s;
-            ET = es;
-            mxT = d[0] + d[3] + d[4] + d[5] + d[6];
-            myT = d[1] + d[3] - d[4] + d[7] + d[8];
-            mzT = d[2] + d[5] - d[6] + d[7] - d[8];
         }
-        double sf = (double)sfT, E = (double)ET;
-        if (sizeof(T) == 4) {
-            sf += ph.n_ref;
-            E += ph.eps_ref;
-        }
-        const double Mx = (double)mxT * ph.c_l, My = (double)myT * ph.c_l, Mz = (double)mzT * ph.c_l;
-        const double sq = sqrt(4.0 * E * E - 3.0 * (Mx * Mx + My * My + Mz * Mz));
-        const double eps = sq - E;
-        const double D = 3.0 * E + eps;
-        const double r3 = 3.0 / D;
-        const double bx = Mx * r3, by = My * r3, bz = Mz * r3;
-        const double b2 = bx * bx + by * by + bz * bz;
-        const double gam2 = 1.0 / (1.0 - b2);
-        // ---- equilibria (as stored: FP64 values or FP32 deviations) ----
-        T feq[19], geq[19];
+        T ae, gbx, gby, gbz;
+        g_eq_adjoint<T>(mug, epst, bx, by, bz, b2, gam2, c.inv_cl, c.inv_cl2, ae, gbx, gby, gbz);
+        // ---- phase 2: f -- gather, S, f part of dL/dtau and of the adjoint
+#pragma unroll
+        for (int i = 0; i < 19; ++i)
+            h[i] = (bounced >> i) & 1u ? A[opp(i) * S + idx] : A[i * S + idx + o.src(i)];
+        T dS = h[0];
+#pragma unroll
+        for (int i = 1; i < 19; ++i) dS += h[i];
+        const T Sfull = (sizeof(T) == 8) ? dS : dS + c.n_ref;
+        T muf[19];
+#pragma unroll
+        for (int i = 0; i < 19; ++i) muf[i] = load_mu(i);
         {
-            const double q[9] = {bx, by, bz, bx + by, bx - by, bx + bz, bx - bz, by + bz, by - bz};
-            const double eg = eps * gam2;
-            if (sizeof(T) == 8) {
-                feq[0] = (T)(kW0 * sf);
-                geq[0] = (T)(kW0 * (4.0 * eg - eps * (2.0 * ph.inv_cl2 + 1.0) - 2.0 * eg * b2 * ph.inv_cl2));
-            } else {
-                feq[0] = (T)(kW0 * (double)sfT);
-                geq[0] = (T)(kW0 * ((eps - ph.eps_ref) * (3.0 - 2.0 * ph.inv_cl2) + eg * b2 * (4.0 - 2.0 * ph.inv_cl2)));
-            }
+            const T fa = 3 * Sfull * c.inv_cl;
+            tacc += muf[0] * (h[0] - (T)kW0 * dS);
 #pragma unroll
             for (int p = 0; p < 9; ++p) {
-                const double w = pair_w(p);
-                const double fb = (sizeof(T) == 8) ? sf : (double)sfT;
-                const double fa = 3.0 * sf * q[p] * ph.inv_cl;
-                feq[2 * p + 1] = (T)(w * (fb + fa));
-                feq[2 * p + 2] = (T)(w * (fb - fa));
-                const double e0 = (sizeof(T) == 8) ? eps : (eps - ph.eps_ref);
-                const double gs = (e0 + eg * (6.0 * q[p] * q[p] - 2.0 * b2)) * ph.inv_cl2;
-                const double ga = 4.0 * eg * q[p] * ph.inv_cl;
-                geq[2 * p + 1] = (T)(w * (gs + ga));
-                geq[2 * p + 2] = (T)(w * (gs - ga));
+                const T w = (T)pair_w(p);
+                const T fs = w * dS, fz = w * fa * q[p];
+                tacc += muf[2 * p + 1] * (h[2 * p + 1] - (fs + fz)) + muf[2 * p + 2] * (h[2 * p + 2] - (fs - fz));
             }
         }
-        // dL/dtau: sum mu (h - eq) / tau^2
-        {
-            T acc = 0;
-#pragma unroll
-            for (int i = 0; i < 19; ++i) acc += mu[i] * (h[i] - feq[i]) + mu[19 + i] * (h[19 + i] - geq[i]);
-            tau_acc += (double)acc * inv_tau2;
-        }
-        // ---- nu = J_C^T mu ----
-        T aS, fbx, fby, fbz, ae, gbx, gby, gbz;
-        f_eq_adjoint_S<T>(mu, (T)sf, (T)bx, (T)by, (T)bz, (T)ph.inv_cl, aS, fbx, fby, fbz);
-        g_eq_adjoint<T>(mu + 19, (T)eps, (T)bx, (T)by, (T)bz, (T)b2, (T)gam2, (T)ph.inv_cl, (T)ph.inv_cl2, ae, gbx,
-                        gby, gbz);
+        tau_acc += (double)tacc * c.inv_tau2;
+        T aS, fbx, fby, fbz;
+        f_eq_adjoint_S<T>(muf, Sfull, bx, by, bz, c.inv_cl, aS, fbx, fby, fbz);
         T vE, vx, vy, vz;
-        recovery_adjoint<T>(ae, fbx + gbx, fby + gby, fbz + gbz, (T)E, (T)sq, (T)D, (T)bx, (T)by, (T)bz, (T)Mx,
-                            (T)My, (T)Mz, vE, vx, vy, vz);
-        const T om = (T)ph.omega, omw = (T)(1.0 - ph.omega);
-        const T cl = (T)ph.c_l;
-        T nu[38];
-        const T nuS = om * aS;
-        const T nuE = om * vE;
-        nu[0] = omw * mu[0] + nuS;
-        nu[19] = omw * mu[19] + nuE;
+        recovery_adjoint<T>(ae, fbx + gbx, fby + gby, fbz + gbz, Et, sqt, Dt, bx, by, bz, mx, my, mz, vE, vx, vy, vz);
+        // ---- nu = (1 - 1/tau) mu + (1/tau) P^T v, scattered (transpose of the pull) ----
+        const T nuS = c.om * aS, nuE = c.om * vE;
+        auto scatter = [&](int q, int i, T v) {
+            if ((bounced >> i) & 1u)
+                Lout[(q - i + opp(i)) * S + idx] = v;
+            else
+                Lout[q * S + idx + o.src(i)] = v;
+        };
+        Lout[idx] = c.omw * muf[0] + nuS;
+#pragma unroll
+        for (int i = 1; i < 19; ++i) scatter(i, i, c.omw * muf[i] + nuS);
+        Lout[19 * S + idx] = c.omw * mug[0] + nuE;
         {
             const T pm[9] = {vx, vy, vz, vx + vy, vx - vy, vx + vz, vx - vz, vy + vz, vy - vz};
 #pragma unroll
             for (int p = 0; p < 9; ++p) {
-                nu[2 * p + 1] = omw * mu[2 * p + 1] + nuS;
-                nu[2 * p + 2] = omw * mu[2 * p + 2] + nuS;
-                const T t = om * cl * pm[p];
-                nu[20 + 2 * p] = omw * mu[20 + 2 * p] + nuE + t;
-                nu[21 + 2 * p] = omw * mu[21 + 2 * p] + nuE - t;
-            }
-        }
-        // ---- scatter: transpose of the pull with bounce-back ----
-        Lout[idx] = nu[0];
-        Lout[19 * S + idx] = nu[19];
-#pragma unroll
-        for (int i = 1; i < 19; ++i) {
-            if (bounced[i]) {
-                Lout[opp(i) * S + idx] = nu[i];
-                Lout[(19 + opp(i)) * S + idx] = nu[19 + i];
-            } else {
-                const int s = idx + o.src(i);
-                Lout[i * S + s] = nu[i];
-                Lout[(19 + i) * S + s] = nu[19 + i];
+                const T t = c.om * c.c_l * pm[p];
+                scatter(20 + 2 * p, 2 * p + 1, c.omw * mug[2 * p + 1] + nuE + t);
+                scatter(21 + 2 * p, 2 * p + 2, c.omw * mug[2 * p + 2] + nuE - t);
             }
         }
         // populations of x that a ghost plane would pull: nobody reads them
@@ -488,10 +497,21 @@ cudaError_t launch_adjoint_macro(int prec, const Geom& g, const Phys& ph, const 
 template <typename T>
 static void adjoint_step_t(const Geom& g, const Phys& ph, const T* A, const T* Li, T* Lo, double* red, int nb,
                            cudaStream_t st) {
+    AdjConst<T> c;
+    c.om = (T)ph.omega;
+    c.omw = (T)(1.0 - ph.omega);
+    c.c_l = (T)ph.c_l;
+    c.inv_cl = (T)ph.inv_cl;
+    c.inv_cl2 = (T)ph.inv_cl2;
+    c.n_ref = (T)ph.n_ref;
+    c.g0a = (T)(3.0 - 2.0 * ph.inv_cl2);
+    c.g0b = (T)(4.0 - 2.0 * ph.inv_cl2);
+    c.eps_ref = ph.eps_ref;
+    c.inv_tau2 = ph.omega * ph.omega;
     switch (g.xbc) {
-        case XBC_PERIODIC: k_adjoint_step<T, XBC_PERIODIC><<<nb, 128, 0, st>>>(A, Li, Lo, g, ph, red); break;
-        case XBC_INFLOW_OUTFLOW: k_adjoint_step<T, XBC_INFLOW_OUTFLOW><<<nb, 128, 0, st>>>(A, Li, Lo, g, ph, red); break;
-        default: k_adjoint_step<T, XBC_OUTFLOW_BOTH><<<nb, 128, 0, st>>>(A, Li, Lo, g, ph, red); break;
+        case XBC_PERIODIC: k_adjoint_step<T, XBC_PERIODIC><<<nb, 128, 0, st>>>(A, Li, Lo, g, ph, c, red); break;
+        case XBC_INFLOW_OUTFLOW: k_adjoint_step<T, XBC_INFLOW_OUTFLOW><<<nb, 128, 0, st>>>(A, Li, Lo, g, ph, c, red); break;
+        default: k_adjoint_step<T, XBC_OUTFLOW_BOTH><<<nb, 128, 0, st>>>(A, Li, Lo, g, ph, c, red); break;
     }
 }
 

@@ -58,6 +58,14 @@ __device__ __forceinline__ bool below_one(double v) {
     long long b = __double_as_longlong(v);
     return b >= 0 && b < 0x3FF0000000000000ll;
 }
+__device__ __forceinline__ bool pos_finite(float v) {
+    int b = __float_as_int(v);
+    return b > 0 && b < 0x7F800000;
+}
+__device__ __forceinline__ bool below_one(float v) {
+    int b = __float_as_int(v);
+    return b >= 0 && b < 0x3F800000;
+}
 
 // Offsets (in cells) from cell (x, y, z) to the source x - e of a pull, for
 // the components -1 / 0 / +1 of e, with periodic wrap.  For a non-periodic x
@@ -95,7 +103,9 @@ __device__ __forceinline__ void cell_coords(const Geom& g, int idx, int& x, int&
 }
 
 // Warp-aggregated statistics: each warp adds its counts to one of
-// kCounterSlots slots, so no address sees much contention.
+// kCounterSlots slots, so no address sees much contention; the smallest
+// flagged update id of the warp goes to first_bad with one atomicMin, and
+// only when it beats the value already there.
 __device__ __forceinline__ void count_flags(const Counters& c, bool unphys, bool nonpos, unsigned long long bad_id) {
     const unsigned act = __activemask();
     const unsigned mu = __ballot_sync(act, unphys);
@@ -103,7 +113,18 @@ __device__ __forceinline__ void count_flags(const Counters& c, bool unphys, bool
     if ((mu | mp) == 0u) return;
     const int lane = threadIdx.x & 31;
     const int leader = __ffs(act) - 1;
-    if (unphys) atomicMin(c.first_bad, bad_id);
+    if (mu) {
+        unsigned long long id = unphys ? bad_id : ~0ull;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(act, id, off);
+            // lanes outside 'act' return undefined values to shuffles; only
+            // take values from active lanes
+            const int src = lane ^ off;
+            if (((act >> src) & 1u) && o < id) id = o;
+        }
+        if (lane == leader && id < *(volatile unsigned long long*)c.first_bad) atomicMin(c.first_bad, id);
+    }
     if (lane == leader) {
         const unsigned slot = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) & (kCounterSlots - 1);
         if (mu) atomicAdd(c.slots + slot, (unsigned long long)__popc(mu));

@@ -179,8 +179,8 @@ struct Dev32 {
 };
 
 template <int XBC, bool SOLID>
-__global__ void __launch_bounds__(256) k_step_f32(const float* __restrict__ A, float* __restrict__ B, Geom g,
-                                                  Dev32 c, Counters cnt, int count, long long step_index) {
+__global__ void __launch_bounds__(256, 3) k_step_f32(const float* __restrict__ A, float* __restrict__ B, Geom g,
+                                                     Dev32 c, Counters cnt, int count, long long step_index) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= g.N) return;
     int x, y, z;
@@ -194,105 +194,105 @@ __global__ void __launch_bounds__(256) k_step_f32(const float* __restrict__ A, f
         return;
     }
     const PullOffsets o(g, x, y, z);
-    float f[19], gg[19];
+    // outflow ghost planes copy the cell next to them: store twice
+    const int dup = (XBC != XBC_PERIODIC && x == g.nx - 2) ? 1 : ((XBC == XBC_OUTFLOW_BOTH && x == 1) ? -1 : 0);
+    float* Bc = B + idx;
+    auto put = [&](int q, float v) {
+        Bc[q * S] = v;
+        if (dup) Bc[q * S + dup] = v;
+    };
+    const float om = c.omega;
+
+    // ---- phase 1: energy-momentum populations g_i (they alone fix eps, beta) ----
+    float gg[19];
 #pragma unroll
-    for (int i = 0; i < 19; ++i) {
-        const int s = idx + o.src(i);
-        f[i] = __ldg(A + i * S + s);
-        gg[i] = __ldg(A + (19 + i) * S + s);
-    }
+    for (int i = 0; i < 19; ++i) gg[i] = __ldg(A + (19 + i) * S + idx + o.src(i));
     if (SOLID) {
-        if (is_solid(f[0])) {
+        if (is_solid(gg[0])) {  // the cell itself is solid: keep the marker
             const float m = solid_marker_f();
 #pragma unroll
             for (int q = 0; q < 38; ++q) B[q * S + idx] = m;
             return;
         }
 #pragma unroll
-        for (int i = 1; i < 19; ++i) {
-            if (is_solid(f[i])) {
-                f[i] = __ldg(A + opp(i) * S + idx);
-                gg[i] = __ldg(A + (19 + opp(i)) * S + idx);
-            }
-        }
+        for (int i = 1; i < 19; ++i)
+            if (is_solid(gg[i])) gg[i] = __ldg(A + (19 + opp(i)) * S + idx);  // link bounce-back
     }
-    float dS, dE, mxf, myf, mzf;
-    moments_pairs(f, gg, dS, dE, mxf, myf, mzf);
-    mxf *= c.c_l;
-    myf *= c.c_l;
-    mzf *= c.c_l;
-    // ---- FP64 recovery ----
+    float dE = gg[0], d[9];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        dE += gg[2 * p + 1] + gg[2 * p + 2];
+        d[p] = gg[2 * p + 1] - gg[2 * p + 2];
+    }
+    const float mxf = c.c_l * (d[0] + d[3] + d[4] + d[5] + d[6]);
+    const float myf = c.c_l * (d[1] + d[3] - d[4] + d[7] + d[8]);
+    const float mzf = c.c_l * (d[2] + d[5] - d[6] + d[7] - d[8]);
+    // recovery: FP64 for the cancellation-prone root.  E = eps_ref + sum dg
+    // and d4 = E^2 - 3|M|^2/4 in FP64; sqrt(d4) from a binary32 seed and one
+    // FP64 Newton correction (relative error ~1e-14); eps = 2 sqrt(d4) - E.
+    // D = 3E + eps has no cancellation, so beta = 3M/D and 1 - |beta|^2 are
+    // formed in binary32 (the quotient is rounded to binary32 either way).
     const double E = c.eps_ref + (double)dE;
     const double Mx = mxf, My = myf, Mz = mzf;
     const double m2 = fma(Mx, Mx, fma(My, My, Mz * Mz));
-    const double d4 = fma(E, E, -0.75 * m2);  // (4E^2 - 3M^2)/4
+    const double d4 = fma(E, E, -0.75 * m2);
     const float y0 = rsqrtf((float)d4);
     const double s0 = d4 * (double)y0;
-    const double sres = fma(-s0, s0, d4);
-    const double s = fma(sres, (double)(0.5f * y0), s0);  // sqrt(d4), one Newton step
-    const double eps = fma(2.0, s, -E);
-    const double D = fma(3.0, E, eps);
-    const double r0 = (double)(1.0f / (float)D);
-    const double rr = fma(r0, fma(-D, r0, 1.0), r0);  // 1/D, one Newton step
-    const double r3 = 3.0 * rr;
-    const double bx = Mx * r3, by = My * r3, bz = Mz * r3;
-    const double b2 = fma(bx, bx, fma(by, by, bz * bz));
-    const double omb2 = 1.0 - b2;
-    const bool unphys = !(pos_finite((double)c.n_ref + (double)dS) && pos_finite(E) && nonneg_finite(d4) &&
-                          pos_finite(eps) && below_one(b2));
+    const double sq = fma(fma(-s0, s0, d4), (double)(0.5f * y0), s0);
+    const double eps = fma(2.0, sq, -E);
+    const float Df = (float)fma(3.0, E, eps);
     const float deps = (float)(eps - c.eps_ref);
-    // ---- FP32 equilibria and BGK ----
-    const float bxf = (float)bx, byf = (float)by, bzf = (float)bz, b2f = (float)b2;
-    const bool nonpos = nonpositive_eq(bxf, byf, bzf, c.c_l);
-    const float gam2 = 1.0f / (float)omb2;
     const float epsf = (float)eps;
+    const float r3 = 3.0f / Df;
+    const float bx = mxf * r3, by = myf * r3, bz = mzf * r3;
+    const float b2 = fmaf(bx, bx, fmaf(by, by, bz * bz));
+    const float gam2 = 1.0f / (1.0f - b2);
     const float eg = epsf * gam2;
-    const float sfull = c.n_ref + dS;
-    const float om = c.omega;
-    const float qv[9] = {bxf, byf, bzf, bxf + byf, bxf - byf, bxf + bzf, bxf - bzf, byf + bzf, byf - bzf};
-    const float fa = 3.0f * sfull * c.inv_cl;
-    const float k1 = (deps - 2.0f * eg * b2f) * c.inv_cl2;
-    const float k2 = 6.0f * eg * c.inv_cl2;
-    const float k3 = 4.0f * eg * c.inv_cl;
-    float outf[19], outg[19];
+    const float qv[9] = {bx, by, bz, bx + by, bx - by, bx + bz, bx - bz, by + bz, by - bz};
     {
-        const float feq0 = (float)kW0 * dS;
-        outf[0] = fmaf(om, feq0 - f[0], f[0]);
-        const float geq0 = (float)kW0 * (deps * c.g0a + eg * b2f * c.g0b);
-        outg[0] = fmaf(om, geq0 - gg[0], gg[0]);
+        const float k1 = (deps - 2.0f * eg * b2) * c.inv_cl2;
+        const float k2 = 6.0f * eg * c.inv_cl2;
+        const float k3 = 4.0f * eg * c.inv_cl;
+        put(19, fmaf(om, (float)kW0 * (deps * c.g0a + eg * b2 * c.g0b) - gg[0], gg[0]));
+#pragma unroll
+        for (int p = 0; p < 9; ++p) {
+            const float w = (float)pair_w(p);
+            const float gsym = w * fmaf(k2, qv[p] * qv[p], k1);
+            const float gasy = w * k3 * qv[p];
+            put(20 + 2 * p, fmaf(om, (gsym + gasy) - gg[2 * p + 1], gg[2 * p + 1]));
+            put(21 + 2 * p, fmaf(om, (gsym - gasy) - gg[2 * p + 2], gg[2 * p + 2]));
+        }
     }
+
+    // ---- phase 2: number populations f_i ----
+    float f[19];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) f[i] = __ldg(A + i * S + idx + o.src(i));
+    if (SOLID) {
+#pragma unroll
+        for (int i = 1; i < 19; ++i)
+            if (is_solid(f[i])) f[i] = __ldg(A + opp(i) * S + idx);
+    }
+    float dS = f[0];
+#pragma unroll
+    for (int i = 1; i < 19; ++i) dS += f[i];
+    const float sfull = c.n_ref + dS;
+    const float fa = 3.0f * sfull * c.inv_cl;
+    put(0, fmaf(om, (float)kW0 * dS - f[0], f[0]));
 #pragma unroll
     for (int p = 0; p < 9; ++p) {
         const float w = (float)pair_w(p);
         const float fsym = w * dS;
         const float fasy = w * fa * qv[p];
-        outf[2 * p + 1] = fmaf(om, (fsym + fasy) - f[2 * p + 1], f[2 * p + 1]);
-        outf[2 * p + 2] = fmaf(om, (fsym - fasy) - f[2 * p + 2], f[2 * p + 2]);
-        const float gsym = w * fmaf(k2, qv[p] * qv[p], k1);
-        const float gasy = w * k3 * qv[p];
-        outg[2 * p + 1] = fmaf(om, (gsym + gasy) - gg[2 * p + 1], gg[2 * p + 1]);
-        outg[2 * p + 2] = fmaf(om, (gsym - gasy) - gg[2 * p + 2], gg[2 * p + 2]);
+        put(2 * p + 1, fmaf(om, (fsym + fasy) - f[2 * p + 1], f[2 * p + 1]));
+        put(2 * p + 2, fmaf(om, (fsym - fasy) - f[2 * p + 2], f[2 * p + 2]));
     }
-#pragma unroll
-    for (int i = 0; i < 19; ++i) {
-        B[i * S + idx] = outf[i];
-        B[(19 + i) * S + idx] = outg[i];
+    if (count) {
+        const bool unphys =
+            !(pos_finite(sfull) && pos_finite(E) && nonneg_finite(d4) && pos_finite(eps) && below_one(b2));
+        const bool nonpos = nonpositive_eq(bx, by, bz, c.c_l);
+        count_flags(cnt, unphys, nonpos, (unsigned long long)step_index * (unsigned long long)g.N + idx);
     }
-    if (XBC != XBC_PERIODIC && x == g.nx - 2) {
-#pragma unroll
-        for (int i = 0; i < 19; ++i) {
-            B[i * S + idx + 1] = outf[i];
-            B[(19 + i) * S + idx + 1] = outg[i];
-        }
-    }
-    if (XBC == XBC_OUTFLOW_BOTH && x == 1) {
-#pragma unroll
-        for (int i = 0; i < 19; ++i) {
-            B[i * S + idx - 1] = outf[i];
-            B[(19 + i) * S + idx - 1] = outg[i];
-        }
-    }
-    if (count) count_flags(cnt, unphys, nonpos, (unsigned long long)step_index * (unsigned long long)g.N + idx);
 }
 
 // ---------------------------------------------------------------------------

@@ -43,14 +43,27 @@ class RLB:
             self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
             self.ctx = N.rlb_create(self.params, self.stream.cuda_stream, self.ws, self.ws_bytes)
 
+    @staticmethod
+    def reference_value(values) -> float:
+        """Uniform FP32 deviation reference for a positive field: the value r that
+        minimises the largest relative deviation max |v - r| / v over the field,
+        r = 2 v_min v_max / (v_min + v_max).  Binary32 rounds the stored deviation
+        v - r, so this bounds the relative rounding of every cell by the same
+        factor on both ends of the range."""
+        v = np.asarray(values, dtype=np.float64)
+        lo, hi = float(v.min()), float(v.max())
+        return 2.0 * lo * hi / (lo + hi)
+
     @classmethod
     def from_workload(cls, w, precision="fp64", device=None, n_ref=None, eps_ref=None, **kw):
-        """Context for a ``workloads.Workload``; the FP32 reference defaults to the
-        volume means of the initial fields over non-solid cells."""
-        if n_ref is None or eps_ref is None:
-            m = np.ones(w.eps.shape, bool) if w.solid is None else (w.solid == 0)
-            n_ref = float(np.mean(w.n[m])) if n_ref is None else n_ref
-            eps_ref = float(np.mean(w.eps[m])) if eps_ref is None else eps_ref
+        """Context for a ``workloads.Workload``; the FP32 reference defaults to
+        ``reference_value`` of the initial fields over the non-solid cells (and the
+        inflow state)."""
+        m = np.ones(w.eps.shape, bool) if w.solid is None else (w.solid == 0)
+        if n_ref is None:
+            n_ref = cls.reference_value(np.append(w.n[m], w.n_in))
+        if eps_ref is None:
+            eps_ref = cls.reference_value(np.append(w.eps[m], w.eps_in))
         xbc = {0: "periodic", 1: "inflow_outflow", 2: "outflow_both"}[w.xbc]
         return cls(w.nx, w.ny, w.nz, w.tau, w.c_l, precision, xbc, w.n_in, w.eps_in, w.beta_in, n_ref, eps_ref,
                    device=device, **kw)

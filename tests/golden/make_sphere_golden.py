@@ -47,8 +47,8 @@ def main():
     n, e, b, bad = oracle.macro(p, st, w.solid)
     cells = sample_cells(w)
     rec = {
-        "_what": "FP64 oracle, sphere_3d workload (200x100x100, tau 0.8, beta_in 0.5), macroscopic fields at "
-                 "sampled cells after the given number of steps",
+        "_what": "FP64 oracle, sphere_3d workload (200x100x100, tau 0.8, beta_in 0.5, interior eps 1, n 0.3), "
+                 "macroscopic fields at sampled cells after the given number of steps",
         "steps": steps,
         "oracle_seconds": dt,
         "oracle_threads": oracle.get_threads(),
