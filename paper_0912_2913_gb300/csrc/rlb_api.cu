@@ -101,7 +101,7 @@ void layout(const rlb_params* p, long long* S, int* elem, size_t* state_bytes) {
     *state_bytes = (size_t)38 * (size_t)(*S) * (size_t)(*elem);
 }
 
-size_t counters_bytes() { return align_up(sizeof(unsigned long long) * (2 * kCounterSlots + 2), kAlign); }
+size_t counters_bytes() { return align_up(sizeof(unsigned long long) * (2 * kCounterSlots + 3), kAlign); }
 size_t red_bytes() { return align_up(sizeof(double) * 4 * kAdjBlocksMax, kAlign); }
 
 size_t workspace_size(const rlb_params* p) {
@@ -116,7 +116,7 @@ rlb_status reset_counters(rlb_ctx* c) {
     RLB_CUDA(c, cudaMemsetAsync(c->cnt.slots, 0, sizeof(unsigned long long) * 2 * kCounterSlots, c->stream),
              "reset counters");
     RLB_CUDA(c, cudaMemsetAsync(c->cnt.first_bad, 0xff, sizeof(unsigned long long), c->stream), "reset counters");
-    RLB_CUDA(c, cudaMemsetAsync(c->cnt.macro_bad, 0, sizeof(unsigned long long), c->stream), "reset counters");
+    RLB_CUDA(c, cudaMemsetAsync(c->cnt.macro_bad, 0, 2 * sizeof(unsigned long long), c->stream), "reset counters");
     return RLB_OK;
 }
 
@@ -124,15 +124,6 @@ rlb_status after_launch(rlb_ctx* c, cudaError_t e, const char* where) {
     c->launches += last_launch_count();
     if (e != cudaSuccess) return cuda_fail(c, e, where);
     return RLB_OK;
-}
-
-bool is_device_ptr(const void* p) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
 }  // namespace
@@ -190,6 +181,10 @@ rlb_status rlb_create(const rlb_params* p, void* stream, void* workspace, size_t
     g.N = p->nx * p->ny * p->nz;
     g.S = S;
     g.xbc = p->xbc;
+    {
+        const char* t = getenv("RLB_TMA");
+        g.tma = (t && t[0] == '0') ? 0 : 1;
+    }
     Phys& ph = c->ph;
     ph.tau = p->tau;
     ph.omega = 1.0 / p->tau;
@@ -222,6 +217,7 @@ rlb_status rlb_create(const rlb_params* p, void* stream, void* workspace, size_t
     c->cnt.slots = (unsigned long long*)(base + 2 * sb);
     c->cnt.first_bad = c->cnt.slots + 2 * kCounterSlots;
     c->cnt.macro_bad = c->cnt.first_bad + 1;
+    c->cnt.pipe_err = c->cnt.first_bad + 2;
     c->red = (double*)(base + 2 * sb + counters_bytes());
     s = reset_counters(c);
     if (s != RLB_OK) {
@@ -377,9 +373,9 @@ rlb_status rlb_macro(rlb_ctx* c, const void* state, double* n, double* eps, doub
 
 rlb_status rlb_stats(rlb_ctx* c, int64_t* steps, int64_t* n_unphysical, int64_t* first_bad, int64_t* n_nonpositive_eq) {
     RLB_LATCHED(c);
-    unsigned long long* h = (unsigned long long*)malloc(sizeof(unsigned long long) * (2 * kCounterSlots + 1));
+    unsigned long long* h = (unsigned long long*)malloc(sizeof(unsigned long long) * (2 * kCounterSlots + 3));
     if (!h) return fail(c, RLB_ERR_OOM, "host allocation failed");
-    cudaError_t e = cudaMemcpyAsync(h, c->cnt.slots, sizeof(unsigned long long) * (2 * kCounterSlots + 1),
+    cudaError_t e = cudaMemcpyAsync(h, c->cnt.slots, sizeof(unsigned long long) * (2 * kCounterSlots + 3),
                                     cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
@@ -392,7 +388,12 @@ rlb_status rlb_stats(rlb_ctx* c, int64_t* steps, int64_t* n_unphysical, int64_t*
         p += h[kCounterSlots + i];
     }
     const unsigned long long fb = h[2 * kCounterSlots];
+    const unsigned long long perr = h[2 * kCounterSlots + 2];
     free(h);
+    if (perr) {
+        c->err = cudaErrorLaunchTimeout;
+        return fail(c, RLB_ERR_CUDA, "a staged kernel timed out waiting for its bulk copies (%llu CTAs)", perr);
+    }
     if (steps) *steps = c->steps;
     if (n_unphysical) *n_unphysical = (int64_t)u;
     if (first_bad) *first_bad = fb == ~0ull ? -1 : (int64_t)fb;

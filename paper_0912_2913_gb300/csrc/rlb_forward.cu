@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "rlb_collide.cuh"
 #include "rlb_device.cuh"
 
 namespace rlb {
@@ -172,11 +173,6 @@ __global__ void __launch_bounds__(128) k_step_f64(const double* __restrict__ A, 
 //   dg_0 = w_0 [d_eps (3 - 2/c_l^2) + eps gamma^2 b2 (4 - 2/c_l^2)]
 // with dS = sum df, d_eps = eps - eps_ref (FP64, then rounded).
 // ---------------------------------------------------------------------------
-struct Dev32 {
-    float omega, omw, c_l, inv_cl, inv_cl2, n_ref;
-    float g0a, g0b;  // 3 - 2/c_l^2 and 4 - 2/c_l^2
-    double eps_ref;
-};
 
 template <int XBC, bool SOLID>
 __global__ void __launch_bounds__(256, 3) k_step_f32(const float* __restrict__ A, float* __restrict__ B, Geom g,
@@ -194,105 +190,26 @@ __global__ void __launch_bounds__(256, 3) k_step_f32(const float* __restrict__ A
         return;
     }
     const PullOffsets o(g, x, y, z);
-    // outflow ghost planes copy the cell next to them: store twice
     const int dup = (XBC != XBC_PERIODIC && x == g.nx - 2) ? 1 : ((XBC == XBC_OUTFLOW_BOTH && x == 1) ? -1 : 0);
     float* Bc = B + idx;
     auto put = [&](int q, float v) {
         Bc[q * S] = v;
         if (dup) Bc[q * S + dup] = v;
     };
-    const float om = c.omega;
-
-    // ---- phase 1: energy-momentum populations g_i (they alone fix eps, beta) ----
-    float gg[19];
+    if (SOLID && is_solid(__ldg(A + 19 * S + idx))) {  // the cell itself is solid: keep the marker
+        const float m = solid_marker_f();
 #pragma unroll
-    for (int i = 0; i < 19; ++i) gg[i] = __ldg(A + (19 + i) * S + idx + o.src(i));
-    if (SOLID) {
-        if (is_solid(gg[0])) {  // the cell itself is solid: keep the marker
-            const float m = solid_marker_f();
-#pragma unroll
-            for (int q = 0; q < 38; ++q) B[q * S + idx] = m;
-            return;
-        }
-#pragma unroll
-        for (int i = 1; i < 19; ++i)
-            if (is_solid(gg[i])) gg[i] = __ldg(A + (19 + opp(i)) * S + idx);  // link bounce-back
+        for (int q = 0; q < 38; ++q) Bc[q * S] = m;
+        return;
     }
-    float dE = gg[0], d[9];
-#pragma unroll
-    for (int p = 0; p < 9; ++p) {
-        dE += gg[2 * p + 1] + gg[2 * p + 2];
-        d[p] = gg[2 * p + 1] - gg[2 * p + 2];
-    }
-    const float mxf = c.c_l * (d[0] + d[3] + d[4] + d[5] + d[6]);
-    const float myf = c.c_l * (d[1] + d[3] - d[4] + d[7] + d[8]);
-    const float mzf = c.c_l * (d[2] + d[5] - d[6] + d[7] - d[8]);
-    // recovery: FP64 for the cancellation-prone root.  E = eps_ref + sum dg
-    // and d4 = E^2 - 3|M|^2/4 in FP64; sqrt(d4) from a binary32 seed and one
-    // FP64 Newton correction (relative error ~1e-14); eps = 2 sqrt(d4) - E.
-    // D = 3E + eps has no cancellation, so beta = 3M/D and 1 - |beta|^2 are
-    // formed in binary32 (the quotient is rounded to binary32 either way).
-    const double E = c.eps_ref + (double)dE;
-    const double Mx = mxf, My = myf, Mz = mzf;
-    const double m2 = fma(Mx, Mx, fma(My, My, Mz * Mz));
-    const double d4 = fma(E, E, -0.75 * m2);
-    const float y0 = rsqrtf((float)d4);
-    const double s0 = d4 * (double)y0;
-    const double sq = fma(fma(-s0, s0, d4), (double)(0.5f * y0), s0);
-    const double eps = fma(2.0, sq, -E);
-    const float Df = (float)fma(3.0, E, eps);
-    const float deps = (float)(eps - c.eps_ref);
-    const float epsf = (float)eps;
-    const float r3 = 3.0f / Df;
-    const float bx = mxf * r3, by = myf * r3, bz = mzf * r3;
-    const float b2 = fmaf(bx, bx, fmaf(by, by, bz * bz));
-    const float gam2 = 1.0f / (1.0f - b2);
-    const float eg = epsf * gam2;
-    const float qv[9] = {bx, by, bz, bx + by, bx - by, bx + bz, bx - bz, by + bz, by - bz};
-    {
-        const float k1 = (deps - 2.0f * eg * b2) * c.inv_cl2;
-        const float k2 = 6.0f * eg * c.inv_cl2;
-        const float k3 = 4.0f * eg * c.inv_cl;
-        put(19, fmaf(om, (float)kW0 * (deps * c.g0a + eg * b2 * c.g0b) - gg[0], gg[0]));
-#pragma unroll
-        for (int p = 0; p < 9; ++p) {
-            const float w = (float)pair_w(p);
-            const float gsym = w * fmaf(k2, qv[p] * qv[p], k1);
-            const float gasy = w * k3 * qv[p];
-            put(20 + 2 * p, fmaf(om, (gsym + gasy) - gg[2 * p + 1], gg[2 * p + 1]));
-            put(21 + 2 * p, fmaf(om, (gsym - gasy) - gg[2 * p + 2], gg[2 * p + 2]));
-        }
-    }
-
-    // ---- phase 2: number populations f_i ----
-    float f[19];
-#pragma unroll
-    for (int i = 0; i < 19; ++i) f[i] = __ldg(A + i * S + idx + o.src(i));
-    if (SOLID) {
-#pragma unroll
-        for (int i = 1; i < 19; ++i)
-            if (is_solid(f[i])) f[i] = __ldg(A + opp(i) * S + idx);
-    }
-    float dS = f[0];
-#pragma unroll
-    for (int i = 1; i < 19; ++i) dS += f[i];
-    const float sfull = c.n_ref + dS;
-    const float fa = 3.0f * sfull * c.inv_cl;
-    put(0, fmaf(om, (float)kW0 * dS - f[0], f[0]));
-#pragma unroll
-    for (int p = 0; p < 9; ++p) {
-        const float w = (float)pair_w(p);
-        const float fsym = w * dS;
-        const float fasy = w * fa * qv[p];
-        put(2 * p + 1, fmaf(om, (fsym + fasy) - f[2 * p + 1], f[2 * p + 1]));
-        put(2 * p + 2, fmaf(om, (fsym - fasy) - f[2 * p + 2], f[2 * p + 2]));
-    }
-    if (count) {
-        const bool unphys =
-            !(pos_finite(sfull) && pos_finite(E) && nonneg_finite(d4) && pos_finite(eps) && below_one(b2));
-        const bool nonpos = nonpositive_eq(bx, by, bz, c.c_l);
-        count_flags(cnt, unphys, nonpos, (unsigned long long)step_index * (unsigned long long)g.N + idx);
-    }
+    auto fetch = [&](int q, int i) {
+        float v = __ldg(A + q * S + idx + o.src(i));
+        if (SOLID && i > 0 && is_solid(v)) v = __ldg(A + (q - i + opp(i)) * S + idx);  // link bounce-back
+        return v;
+    };
+    bool unphys, nonpos;
+    collide_cell_f32(fetch, put, c, unphys, nonpos);
+    if (count) count_flags(cnt, unphys, nonpos, (unsigned long long)step_index * (unsigned long long)g.N + idx);
 }
 
 // ---------------------------------------------------------------------------
@@ -428,6 +345,20 @@ __global__ void k_check_solid_planes(Geom g, const uint8_t* __restrict__ solid, 
 // ---------------------------------------------------------------------------
 static inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+Dev32 make_dev32(const Phys& ph) {
+    Dev32 c;
+    c.omega = (float)ph.omega;
+    c.omw = (float)(1.0 - ph.omega);
+    c.c_l = (float)ph.c_l;
+    c.inv_cl = (float)ph.inv_cl;
+    c.inv_cl2 = (float)ph.inv_cl2;
+    c.n_ref = (float)ph.n_ref;
+    c.g0a = (float)(3.0 - 2.0 * ph.inv_cl2);
+    c.g0b = (float)(4.0 - 2.0 * ph.inv_cl2);
+    c.eps_ref = ph.eps_ref;
+    return c;
+}
+
 cudaError_t launch_init(int prec, const Geom& g, const Phys& ph, const double* n, const double* eps,
                         const double* beta, const uint8_t* solid, void* A, void* B, cudaStream_t st) {
     g_last_launches = 1;
@@ -445,16 +376,10 @@ static void launch_step_t(int prec, const Geom& g, const Phys& ph, const void* A
         k_step_f64<XBC, SOLID><<<blocks_for(g.N, 128), 128, 0, st>>>((const double*)A, (double*)B, g, ph, cnt,
                                                                       count ? 1 : 0, step_index);
     } else {
-        Dev32 c;
-        c.omega = (float)ph.omega;
-        c.omw = (float)(1.0 - ph.omega);
-        c.c_l = (float)ph.c_l;
-        c.inv_cl = (float)ph.inv_cl;
-        c.inv_cl2 = (float)ph.inv_cl2;
-        c.n_ref = (float)ph.n_ref;
-        c.g0a = (float)(3.0 - 2.0 * ph.inv_cl2);
-        c.g0b = (float)(4.0 - 2.0 * ph.inv_cl2);
-        c.eps_ref = ph.eps_ref;
+        const Dev32 c = make_dev32(ph);
+        if (g.tma && launch_step_f32_tma(g, c, (const float*)A, (float*)B, cnt, count, step_index, st) == cudaSuccess)
+            return;
+        cudaGetLastError();
         k_step_f32<XBC, SOLID><<<blocks_for(g.N, 256), 256, 0, st>>>((const float*)A, (float*)B, g, c, cnt,
                                                                       count ? 1 : 0, step_index);
     }

@@ -23,6 +23,7 @@ struct Geom {
     int N;       // nx * ny * nz (< 2^31)
     long long S; // plane stride in elements (N rounded up to a multiple of 64)
     int xbc;
+    int tma;     // 1: use the TMA-staged FP32 step where the lattice allows it
 };
 
 // Physical parameters, with the derived constants the kernels use.
@@ -33,11 +34,19 @@ struct Phys {
     double n_ref, eps_ref;  // FP32 deviation reference (beta = 0)
 };
 
+// Binary32 constants of the FP32 deviation step.
+struct Dev32 {
+    float omega, omw, c_l, inv_cl, inv_cl2, n_ref;
+    float g0a, g0b;  // 3 - 2/c_l^2 and 4 - 2/c_l^2
+    double eps_ref;
+};
+
 // Device-side statistics of a run (see rlb_stats).
 struct Counters {
     unsigned long long* slots;      // [2][kCounterSlots]: unphysical, non-positive equilibria
     unsigned long long* first_bad;  // min over flagged updates of step*N + cell
     unsigned long long* macro_bad;  // cells flagged by the last macro evaluation
+    unsigned long long* pipe_err;   // set when a staged kernel gave up waiting for its copies
 };
 
 // Launchers (return the launch error, enqueue on 'stream').
@@ -47,6 +56,12 @@ cudaError_t launch_step(int prec, const Geom& g, const Phys& ph, const void* A, 
                         bool count, long long step_index, cudaStream_t stream);
 cudaError_t launch_macro(int prec, const Geom& g, const Phys& ph, const void* A, double* n, double* eps,
                          double* beta, Counters cnt, cudaStream_t stream);
+// TMA-staged FP32 step; returns cudaErrorNotSupported when the lattice does
+// not meet its alignment / shared-memory conditions (caller falls back).
+cudaError_t launch_step_f32_tma(const Geom& g, const Dev32& c, const float* A, float* B, Counters cnt, bool count,
+                                long long step_index, cudaStream_t stream);
+Dev32 make_dev32(const Phys& ph);
+
 cudaError_t launch_check_solid_planes(const Geom& g, const uint8_t* solid, unsigned long long* flag,
                                       cudaStream_t stream);
 
