@@ -175,6 +175,15 @@ RLB_API rlb_status rlb_adjoint_fields(rlb_ctx* ctx, const double* n0, const doub
                               const void* lam0, double* dL_dn0, double* dL_deps0, double* dL_dbeta0,
                               double* dL_dbeta_in_accum);
 
+/* Diagnostic: the integer-pipe binary32 <-> binary64 conversions that the
+ * FP32 deviation kernels use in their recovery, applied elementwise on the
+ * current device (legacy default stream, synchronises): f2d_out[k] =
+ * (double)f_in[k], d2f_out[k] = (float)d_in[k] rounded to nearest even.  All
+ * pointers device, n >= 0.  Exact for values whose results are normal
+ * numbers, zero, inf or NaN; binary32 subnormal results flush to zero.      */
+RLB_API rlb_status rlb_selftest_conversions(const float* f_in, const double* d_in, int64_t n, double* f2d_out,
+                                            float* d2f_out);
+
 /* Wait for the context's stream; returns a latched or new CUDA error.       */
 RLB_API rlb_status rlb_sync(rlb_ctx* ctx);
 

@@ -25,7 +25,7 @@ EXPORTS = (
     "rlb_state_layout", "rlb_workspace_bytes", "rlb_create", "rlb_destroy", "rlb_init_fields", "rlb_step",
     "rlb_step_into", "rlb_state_ptr", "rlb_save_state", "rlb_load_state", "rlb_macro", "rlb_stats",
     "rlb_adjoint_macro", "rlb_adjoint_step", "rlb_adjoint_fields", "rlb_sync", "rlb_status_str", "rlb_last_error",
-    "rlb_launch_count",
+    "rlb_launch_count", "rlb_selftest_conversions",
 )
 
 
@@ -90,6 +90,7 @@ def load(build_if_missing: bool = True):
             "rlb_status_str": ([ctypes.c_int], ctypes.c_char_p),
             "rlb_last_error": ([vp], ctypes.c_char_p),
             "rlb_launch_count": ([vp], i64),
+            "rlb_selftest_conversions": ([vp, vp, i64, vp, vp], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -219,6 +220,10 @@ def rlb_status_str(status: int) -> str:
 
 def rlb_last_error(ctx=None) -> str:
     return load().rlb_last_error(ctx).decode(errors="replace")
+
+
+def rlb_selftest_conversions(f_in, d_in, n, f2d_out, d2f_out) -> None:
+    _check(load().rlb_selftest_conversions(_ptr(f_in), _ptr(d_in), int(n), _ptr(f2d_out), _ptr(d2f_out)))
 
 
 def rlb_launch_count(ctx) -> int:

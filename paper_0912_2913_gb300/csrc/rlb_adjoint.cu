@@ -280,18 +280,19 @@ __global__ void __launch_bounds__(128, (sizeof(T) == 4 ? 4 : 2))
             epst = eps;
             e0 = eps;
         } else {
-            const double E = c.eps_ref + (double)dE;
-            const double Mx = mx, My = my, Mz = mz;
+            // as in the forward FP32 collision: FP64 root, conversions on the ALU
+            const double E = c.eps_ref + f2d(dE);
+            const double Mx = f2d(mx), My = f2d(my), Mz = f2d(mz);
             const double d4 = fma(E, E, -0.75 * fma(Mx, Mx, fma(My, My, Mz * Mz)));
-            const float y0 = rsqrtf((float)d4);
-            const double s0 = d4 * (double)y0;
-            const double s = fma(fma(-s0, s0, d4), (double)(0.5f * y0), s0);
+            const float y0 = rsqrtf(d2f_seed(d4));
+            const double s0 = d4 * f2d(y0);
+            const double s = fma(fma(-s0, s0, d4), f2d(0.5f * y0), s0);
             const double eps = fma(2.0, s, -E);
-            Dt = (float)fma(3.0, E, eps);
-            e0 = (float)(eps - c.eps_ref);
-            epst = (float)eps;
-            Et = (float)E;
-            sqt = (float)(2.0 * s);
+            Dt = d2f(fma(3.0, E, eps));
+            e0 = d2f(eps - c.eps_ref);
+            epst = d2f(eps);
+            Et = d2f(E);
+            sqt = d2f(2.0 * s);
             const float r3 = 3.0f / Dt;
             bx = mx * r3;
             by = my * r3;

@@ -431,6 +431,14 @@ rlb_status rlb_adjoint_fields(rlb_ctx* c, const double* n0, const double* eps0, 
                         "adjoint_fields");
 }
 
+rlb_status rlb_selftest_conversions(const float* f_in, const double* d_in, int64_t n, double* f2d_out,
+                                    float* d2f_out) {
+    if (n < 0 || (n > 0 && (!f_in || !d_in || !f2d_out || !d2f_out))) return fail(nullptr, RLB_ERR_ARG, "bad arguments");
+    cudaError_t e = launch_conversions(f_in, d_in, n, f2d_out, d2f_out);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "selftest_conversions");
+    return RLB_OK;
+}
+
 rlb_status rlb_sync(rlb_ctx* c) {
     RLB_LATCHED(c);
     RLB_CUDA(c, cudaStreamSynchronize(c->stream), "sync");

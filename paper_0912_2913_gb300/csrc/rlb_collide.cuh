@@ -42,17 +42,18 @@ __device__ __forceinline__ void collide_cell_f32(Fetch fetch, Put put, const Dev
     // Newton correction (relative error ~1e-14), eps = 2 sqrt(d4) - E.
     // D = 3E + eps has no cancellation, so beta = 3M/D and 1 - |beta|^2 are
     // formed in binary32 (the quotient is rounded to binary32 either way).
-    const double E = c.eps_ref + (double)dE;
-    const double Mx = mxf, My = myf, Mz = mzf;
+    // The binary32 <-> binary64 conversions run on the integer pipe.
+    const double E = c.eps_ref + f2d(dE);
+    const double Mx = f2d(mxf), My = f2d(myf), Mz = f2d(mzf);
     const double m2 = fma(Mx, Mx, fma(My, My, Mz * Mz));
     const double d4 = fma(E, E, -0.75 * m2);
-    const float y0 = rsqrtf((float)d4);
-    const double s0 = d4 * (double)y0;
-    const double sq = fma(fma(-s0, s0, d4), (double)(0.5f * y0), s0);
+    const float y0 = rsqrtf(d2f_seed(d4));
+    const double s0 = d4 * f2d(y0);
+    const double sq = fma(fma(-s0, s0, d4), f2d(0.5f * y0), s0);
     const double eps = fma(2.0, sq, -E);
-    const float Df = (float)fma(3.0, E, eps);
-    const float deps = (float)(eps - c.eps_ref);
-    const float epsf = (float)eps;
+    const float Df = d2f(fma(3.0, E, eps));
+    const float deps = d2f(eps - c.eps_ref);
+    const float epsf = d2f(eps);
     const float r3 = 3.0f / Df;
     const float bx = mxf * r3, by = myf * r3, bz = mzf * r3;
     const float b2 = fmaf(bx, bx, fmaf(by, by, bz * bz));

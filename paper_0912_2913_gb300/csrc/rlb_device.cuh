@@ -67,6 +67,48 @@ __device__ __forceinline__ bool below_one(float v) {
     return b >= 0 && b < 0x3F800000;
 }
 
+// binary32 <-> binary64 conversions on the integer pipe.  On GB300 the
+// hardware conversions issue at the FP64 rate (1/64 of FP32), so the FP32
+// deviation kernels move them to the ALU:
+//  - f2d: exact for normal numbers, zero, inf and NaN; binary32 subnormals
+//    (below 1.2e-38) become zero;
+//  - d2f: round to nearest even, exact as the hardware conversion for
+//    results in the normal binary32 range; results below it flush to zero,
+//    above it become inf;
+//  - d2f_seed: truncation, for seeds of Newton iterations only.
+__device__ __forceinline__ double f2d(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xFFu;
+    const unsigned sign = u & 0x80000000u;
+    const unsigned mhi = (u >> 3) & 0xFFFFFu;
+    unsigned hi = sign | ((e + 896u) << 20) | mhi;
+    unsigned lo = u << 29;
+    if (e == 0u) hi = sign, lo = 0u;
+    if (e == 255u) hi = sign | 0x7FF00000u | mhi;
+    return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ float d2f(double d) {
+    const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7FFu) - 896;
+    const unsigned m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    const unsigned r = lo & 0x1FFFFFFFu;
+    const unsigned up = (r > 0x10000000u) || (r == 0x10000000u && (m & 1u));
+    unsigned bits = sign | ((((unsigned)e << 23) + m) + up);
+    if (e <= 0) bits = sign;
+    if (e >= 255) bits = sign | 0x7F800000u;
+    if (((hi >> 20) & 0x7FFu) == 0x7FFu) bits = sign | 0x7F800000u | (((hi & 0xFFFFFu) | lo) ? 0x400000u : 0u);
+    return __uint_as_float(bits);
+}
+__device__ __forceinline__ float d2f_seed(double d) {
+    const unsigned hi = (unsigned)__double2hiint(d);
+    const int e = (int)((hi >> 20) & 0x7FFu) - 896;
+    unsigned bits = (hi & 0x80000000u) | (((unsigned)e << 23) + ((hi & 0xFFFFFu) << 3));
+    if (e <= 0) bits = hi & 0x80000000u;
+    if (e >= 255) bits = (hi & 0x80000000u) | 0x7F800000u;
+    return __uint_as_float(bits);
+}
+
 // Offsets (in cells) from cell (x, y, z) to the source x - e of a pull, for
 // the components -1 / 0 / +1 of e, with periodic wrap.  For a non-periodic x
 // the interior cells never wrap, so the same formula serves every case.

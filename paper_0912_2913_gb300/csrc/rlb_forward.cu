@@ -331,6 +331,21 @@ __global__ void __launch_bounds__(128) k_macro(const T* __restrict__ A, double* 
     if (bad) atomicAdd(bad_count, 1ull);
 }
 
+__global__ void k_conversions(const float* __restrict__ fi, const double* __restrict__ di, long long n,
+                              double* __restrict__ fo, float* __restrict__ dout) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        fo[k] = f2d(fi[k]);
+        dout[k] = d2f(di[k]);
+    }
+}
+
+cudaError_t launch_conversions(const float* fi, const double* di, long long n, double* fo, float* dout) {
+    if (n > 0) k_conversions<<<1024, 256>>>(fi, di, n, fo, dout);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    return e;
+}
+
 __global__ void k_check_solid_planes(Geom g, const uint8_t* __restrict__ solid, unsigned long long* flag) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int plane = g.ny * g.nz;

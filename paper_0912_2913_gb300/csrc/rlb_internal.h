@@ -62,6 +62,8 @@ cudaError_t launch_step_f32_tma(const Geom& g, const Dev32& c, const float* A, f
                                 long long step_index, cudaStream_t stream);
 Dev32 make_dev32(const Phys& ph);
 
+cudaError_t launch_conversions(const float* fi, const double* di, long long n, double* fo, float* dout);
+
 cudaError_t launch_check_solid_planes(const Geom& g, const uint8_t* solid, unsigned long long* flag,
                                       cudaStream_t stream);
 

@@ -52,32 +52,39 @@ __global__ void __launch_bounds__(512, 1)
     }
     __syncthreads();
 
-    // Producer (thread 0): bulk copies of the source rows of every plane of
-    // tile 'tile' into stage 's'.
+    // Producer (warp 0, all lanes): bulk copies of the source rows of every
+    // plane of tile 'tile' into stage 's'.  Lane i (< 19) copies velocity i of
+    // both f and g (same source rows); wraps use compares, not divisions.
     auto issue = [&](int tile, int s) {
         const int z = tile / tc.tiles_per_z;
         const int y0 = (tile - z * tc.tiles_per_z) * R;
         const int rr = min(R, ny - y0);
         float* st = stages + (size_t)s * stage_elems;
-        mbar_arrive_expect_tx(&bars[s], (unsigned)(38 * rr * nx * 4));
-#pragma unroll 1
-        for (int q = 0; q < 38; ++q) {
-            const int i = q < 19 ? q : q - 19;
-            const int ey = vel_y(i), ez = vel_z(i);
-            const int zs = (z - ez + nz) % nz;
-            const int ys = (y0 - ey + ny) % ny;
+        if (threadIdx.x == 0) mbar_arrive_expect_tx(&bars[s], (unsigned)(38 * rr * nx * 4));
+        __syncwarp();
+        const int i = threadIdx.x;
+        if (i < 19) {
+            int zs = z - vel_z(i);
+            zs = zs < 0 ? zs + nz : (zs >= nz ? zs - nz : zs);
+            int ys = y0 - vel_y(i);
+            ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
             const int seg = min(rr, ny - ys);
-            const float* src = A + q * S + ((long long)zs * ny + ys) * nx;
-            bulk_g2s(st + q * plane_elems, src, (unsigned)(seg * nx * 4), &bars[s]);
-            if (seg < rr)
-                bulk_g2s(st + q * plane_elems + seg * nx, A + q * S + (long long)zs * ny * nx,
-                         (unsigned)((rr - seg) * nx * 4), &bars[s]);
+            const long long row0 = ((long long)zs * ny + ys) * nx;
+            const long long wrap0 = (long long)zs * ny * nx;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int q = i + 19 * h;
+                bulk_g2s(st + q * plane_elems, A + q * S + row0, (unsigned)(seg * nx * 4), &bars[s]);
+                if (seg < rr)
+                    bulk_g2s(st + q * plane_elems + seg * nx, A + q * S + wrap0, (unsigned)((rr - seg) * nx * 4),
+                             &bars[s]);
+            }
         }
     };
 
-    // issued[s]: phase parity pending on stage s, or -1 (thread 0 only)
+    // pend[s]: phase parity pending on stage s, or -1 (warp 0 bookkeeping)
     int pend[4] = {-1, -1, -1, -1};
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
         for (int s = 0; s < K; ++s) {
             const int tile = blockIdx.x + s * gridDim.x;
             if (tile < tc.ntiles) {
@@ -94,7 +101,7 @@ __global__ void __launch_bounds__(512, 1)
         const bool got = mbar_wait(&bars[s], parity);
         ok = __syncthreads_and(got) != 0;
         if (!ok) break;
-        if (threadIdx.x == 0) pend[s] = -1;
+        pend[s] = -1;
         const float* st = stages + (size_t)s * stage_elems;
         const int z = tile / tc.tiles_per_z;
         const int y0 = (tile - z * tc.tiles_per_z) * R;
@@ -136,7 +143,7 @@ __global__ void __launch_bounds__(512, 1)
             if (count) count_flags(cnt, unphys, nonpos, (unsigned long long)step_index * (unsigned long long)g.N + idx);
         }
         __syncthreads();  // every thread is done reading stage s
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < 32) {
             const int next = tile + K * gridDim.x;
             if (next < tc.ntiles) {
                 fence_proxy_async_smem();
