@@ -182,8 +182,12 @@ rlb_status rlb_create(const rlb_params* p, void* stream, void* workspace, size_t
     g.S = S;
     g.xbc = p->xbc;
     {
+        // Tuning knobs (no effect on results): RLB_TMA=1 selects the TMA-staged
+        // FP32 step, RLB_F32_VARIANT the launch variant of the plain one.
         const char* t = getenv("RLB_TMA");
-        g.tma = (t && t[0] == '0') ? 0 : 1;
+        g.tma = (t && t[0] == '1') ? 1 : 0;
+        const char* v = getenv("RLB_F32_VARIANT");
+        g.variant = v ? atoi(v) : 0;
     }
     Phys& ph = c->ph;
     ph.tau = p->tau;

@@ -174,9 +174,11 @@ __global__ void __launch_bounds__(128) k_step_f64(const double* __restrict__ A, 
 // with dS = sum df, d_eps = eps - eps_ref (FP64, then rounded).
 // ---------------------------------------------------------------------------
 
-template <int XBC, bool SOLID>
-__global__ void __launch_bounds__(256, 3) k_step_f32(const float* __restrict__ A, float* __restrict__ B, Geom g,
-                                                     Dev32 c, Counters cnt, int count, long long step_index) {
+// MINB: resident 256-thread blocks per SM the register budget is cut for;
+// PREF: prefetch the rows of the f phase into L2 before the g phase runs.
+template <int XBC, bool SOLID, int MINB, bool PREF>
+__global__ void __launch_bounds__(256, MINB) k_step_f32(const float* __restrict__ A, float* __restrict__ B, Geom g,
+                                                        Dev32 c, Counters cnt, int count, long long step_index) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= g.N) return;
     int x, y, z;
@@ -201,6 +203,10 @@ __global__ void __launch_bounds__(256, 3) k_step_f32(const float* __restrict__ A
 #pragma unroll
         for (int q = 0; q < 38; ++q) Bc[q * S] = m;
         return;
+    }
+    if (PREF) {
+#pragma unroll
+        for (int i = 0; i < 19; ++i) asm volatile("prefetch.global.L2 [%0];" ::"l"(A + i * S + idx + o.src(i)));
     }
     auto fetch = [&](int q, int i) {
         float v = __ldg(A + q * S + idx + o.src(i));
@@ -395,8 +401,14 @@ static void launch_step_t(int prec, const Geom& g, const Phys& ph, const void* A
         if (g.tma && launch_step_f32_tma(g, c, (const float*)A, (float*)B, cnt, count, step_index, st) == cudaSuccess)
             return;
         cudaGetLastError();
-        k_step_f32<XBC, SOLID><<<blocks_for(g.N, 256), 256, 0, st>>>((const float*)A, (float*)B, g, c, cnt,
-                                                                      count ? 1 : 0, step_index);
+        const unsigned nb = blocks_for(g.N, 256);
+        const int cs = count ? 1 : 0;
+        switch (g.variant) {
+            case 1: k_step_f32<XBC, SOLID, 3, true><<<nb, 256, 0, st>>>((const float*)A, (float*)B, g, c, cnt, cs, step_index); break;
+            case 2: k_step_f32<XBC, SOLID, 4, false><<<nb, 256, 0, st>>>((const float*)A, (float*)B, g, c, cnt, cs, step_index); break;
+            case 3: k_step_f32<XBC, SOLID, 4, true><<<nb, 256, 0, st>>>((const float*)A, (float*)B, g, c, cnt, cs, step_index); break;
+            default: k_step_f32<XBC, SOLID, 3, false><<<nb, 256, 0, st>>>((const float*)A, (float*)B, g, c, cnt, cs, step_index); break;
+        }
     }
 }
 

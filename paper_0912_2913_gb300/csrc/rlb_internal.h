@@ -24,6 +24,7 @@ struct Geom {
     long long S; // plane stride in elements (N rounded up to a multiple of 64)
     int xbc;
     int tma;     // 1: use the TMA-staged FP32 step where the lattice allows it
+    int variant; // launch variant of the one-cell-per-thread FP32 step (tuning)
 };
 
 // Physical parameters, with the derived constants the kernels use.

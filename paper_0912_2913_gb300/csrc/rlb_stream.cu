@@ -34,8 +34,8 @@ struct TmaCfg {
     int ntiles;
 };
 
-template <int XBC, bool SOLID>
-__global__ void __launch_bounds__(512, 1)
+template <int XBC, bool SOLID, int MINB>
+__global__ void __launch_bounds__(256, MINB)
     k_step_f32_tma(const float* __restrict__ A, float* __restrict__ B, Geom g, Dev32 c, Counters cnt, int count,
                    long long step_index, TmaCfg tc) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -198,11 +198,12 @@ cudaError_t launch_step_f32_tma(const Geom& g, const Dev32& c, const float* A, f
     tc.tiles_per_z = (g.ny + R - 1) / R;
     tc.ntiles = g.nz * tc.tiles_per_z;
     int threads = ((R * g.nx + 31) / 32) * 32;
-    if (threads > 512) threads = 512;
+    if (threads > 256) threads = 256;
+    const int minb = env_int("RLB_TMA_MINB", 2) >= 3 ? 3 : 2;
     const int ctas_per_sm = env_int("RLB_TMA_CTAS", 1);
     int grid = nsm * ctas_per_sm;
     if (grid > tc.ntiles) grid = tc.ntiles;
-    static size_t smem_set[3] = {0, 0, 0};
+    static size_t smem_set[6] = {0, 0, 0, 0, 0, 0};
     auto run = [&](auto kern, int which) {
         if (smem_set[which] < smem) {
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -210,10 +211,18 @@ cudaError_t launch_step_f32_tma(const Geom& g, const Dev32& c, const float* A, f
         }
         kern<<<grid, threads, smem, st>>>(A, B, g, c, cnt, count ? 1 : 0, step_index, tc);
     };
-    switch (g.xbc) {
-        case XBC_PERIODIC: run(k_step_f32_tma<XBC_PERIODIC, true>, 0); break;
-        case XBC_INFLOW_OUTFLOW: run(k_step_f32_tma<XBC_INFLOW_OUTFLOW, true>, 1); break;
-        default: run(k_step_f32_tma<XBC_OUTFLOW_BOTH, true>, 2); break;
+    if (minb == 3) {
+        switch (g.xbc) {
+            case XBC_PERIODIC: run(k_step_f32_tma<XBC_PERIODIC, true, 3>, 3); break;
+            case XBC_INFLOW_OUTFLOW: run(k_step_f32_tma<XBC_INFLOW_OUTFLOW, true, 3>, 4); break;
+            default: run(k_step_f32_tma<XBC_OUTFLOW_BOTH, true, 3>, 5); break;
+        }
+    } else {
+        switch (g.xbc) {
+            case XBC_PERIODIC: run(k_step_f32_tma<XBC_PERIODIC, true, 2>, 0); break;
+            case XBC_INFLOW_OUTFLOW: run(k_step_f32_tma<XBC_INFLOW_OUTFLOW, true, 2>, 1); break;
+            default: run(k_step_f32_tma<XBC_OUTFLOW_BOTH, true, 2>, 2); break;
+        }
     }
     return cudaGetLastError();
 }

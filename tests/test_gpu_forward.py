@@ -178,9 +178,9 @@ def test_tachyon_lattice_speed():
 
 @pytest.mark.parametrize("shape", [(60, 30, 30, 1), (64, 16, 12, 0), (200, 100, 100, 1), (16, 5, 7, 2)])
 def test_tma_staged_step_equals_plain_step(shape, monkeypatch):
-    """The TMA-staged FP32 step and the one-cell-per-thread FP32 step do the
-    same arithmetic: states agree bit for bit after several steps (tiles that
-    wrap in y, ghost planes, solid cells)."""
+    """The TMA-staged FP32 step and the launch variants of the one-cell-per-
+    thread FP32 step do the same arithmetic: states agree bit for bit after
+    several steps (tiles that wrap in y, ghost planes, solid cells)."""
     nx, ny, nz, xbc = shape
     if xbc == 1:
         w = W.sphere_3d(nx=nx, ny=ny, nz=nz)
@@ -189,14 +189,18 @@ def test_tma_staged_step_equals_plain_step(shape, monkeypatch):
     from paper_0912_2913_gb300 import RLB
 
     states = []
-    for tma in ("1", "0"):
+    for tma, var, minb in (("1", "0", "2"), ("1", "0", "3"), ("0", "0", "2"), ("0", "1", "2"), ("0", "2", "2"),
+                           ("0", "3", "2")):
         monkeypatch.setenv("RLB_TMA", tma)
+        monkeypatch.setenv("RLB_F32_VARIANT", var)
+        monkeypatch.setenv("RLB_TMA_MINB", minb)
         sim = RLB.from_workload(w, "fp32", device="cuda:0").init_fields(w.n, w.eps, w.beta, w.solid).step(7)
         torch.cuda.synchronize()
         states.append((sim.state()[:, :sim.N].clone(), sim.stats()))
         sim.close()
-    assert torch.equal(states[0][0].view(torch.int32), states[1][0].view(torch.int32))
-    assert states[0][1] == states[1][1]
+    for st, stats in states[1:]:
+        assert torch.equal(states[0][0].view(torch.int32), st.view(torch.int32))
+        assert states[0][1] == stats
 
 
 def test_step_into_matches_step():
