@@ -20,8 +20,11 @@ BUILD = os.path.join(HERE, "_build")
 SOURCES = ["rlb_forward.cu", "rlb_stream.cu", "rlb_adjoint.cu", "rlb_api.cu"]
 HEADERS = ["rlb_internal.h", "rlb_device.cuh", "rlb_collide.cuh", "rlb_tma.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
-              "--expt-relaxed-constexpr"]
+# -fmad=false: no implicit a*b+c contraction, so every kernel computes exactly
+# the operations its source writes (fused ones are explicit fma/fmaf calls) and
+# results do not depend on launch variant or register allocation.
+NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC", "-Xcompiler",
+              "-fvisibility=hidden", "--expt-relaxed-constexpr"]
 
 
 def _nvcc() -> str:

@@ -97,12 +97,12 @@ __global__ void __launch_bounds__(128) k_step_f64(const double* __restrict__ A, 
     my *= ph.c_l;
     mz *= ph.c_l;
     // Recovery with eps = 3P: eps = -E + sqrt(4E^2 - 3M^2), beta = 3M/(3E + eps).
-    const double m2 = mx * mx + my * my + mz * mz;
-    const double disc = 4.0 * E * E - 3.0 * m2;
+    const double m2 = fma(mx, mx, fma(my, my, mz * mz));
+    const double disc = fma(4.0 * E, E, -3.0 * m2);
     const double eps = sqrt(disc) - E;
-    const double r3 = 3.0 / (3.0 * E + eps);
+    const double r3 = 3.0 / fma(3.0, E, eps);
     const double bx = mx * r3, by = my * r3, bz = mz * r3;
-    const double b2 = bx * bx + by * by + bz * bz;
+    const double b2 = fma(bx, bx, fma(by, by, bz * bz));
     const double gam2 = 1.0 / (1.0 - b2);
     const bool unphys = !(pos_finite(sf) && pos_finite(E) && nonneg_finite(disc) && pos_finite(eps) && below_one(b2));
     const bool nonpos = nonpositive_eq((float)bx, (float)by, (float)bz, (float)ph.c_l);
@@ -111,12 +111,15 @@ __global__ void __launch_bounds__(128) k_step_f64(const double* __restrict__ A, 
     const double q[9] = {bx, by, bz, bx + by, bx - by, bx + bz, bx - bz, by + bz, by - bz};
     // f^eq_i = w_i S_f (1 + 3 q_i / c_l)     (Eq. equil1s with n gamma = S_f)
     const double fs1 = om * (1.0 / 18.0) * sf, fs2 = om * (1.0 / 36.0) * sf;
-    const double fa = 3.0 * om * sf * ph.inv_cl;
+    const double fa1 = 3.0 * om * sf * ph.inv_cl * (1.0 / 18.0), fa2 = 3.0 * om * sf * ph.inv_cl * (1.0 / 36.0);
     // g^eq_i = w_i [eps/c_l^2 + eps gamma^2 (6 q^2/c_l^2 - 2 b2/c_l^2)] +- w_i eps gamma^2 4 q / c_l
     const double eg = eps * gam2;
     const double k1 = om * (eps - 2.0 * eg * b2) * ph.inv_cl2;
     const double k2 = 6.0 * om * eg * ph.inv_cl2;
     const double k3 = 4.0 * om * eg * ph.inv_cl;
+    const double k1w[2] = {k1 * (1.0 / 18.0), k1 * (1.0 / 36.0)};
+    const double k2w[2] = {k2 * (1.0 / 18.0), k2 * (1.0 / 36.0)};
+    const double k3w[2] = {k3 * (1.0 / 18.0), k3 * (1.0 / 36.0)};
     double outf[19], outg[19];
     outf[0] = fma(omw, f[0], om * kW0 * sf);
     // g_0^eq = w_0 [4 eps gamma^2 - eps (2 + c_l^2)/c_l^2 - 2 eps gamma^2 b2/c_l^2]   (Eq. equil2bs)
@@ -124,13 +127,13 @@ __global__ void __launch_bounds__(128) k_step_f64(const double* __restrict__ A, 
     outg[0] = fma(omw, gg[0], om * g0eq);
 #pragma unroll
     for (int p = 0; p < 9; ++p) {
-        const double w = pair_w(p);
-        const double fsym = p < 3 ? fs1 : fs2;
-        const double fasy = w * fa * q[p];
+        const int cl = p < 3 ? 0 : 1;
+        const double fsym = cl == 0 ? fs1 : fs2;
+        const double fasy = (cl == 0 ? fa1 : fa2) * q[p];
         outf[2 * p + 1] = fma(omw, f[2 * p + 1], fsym + fasy);
         outf[2 * p + 2] = fma(omw, f[2 * p + 2], fsym - fasy);
-        const double gsym = w * fma(k2, q[p] * q[p], k1);
-        const double gasy = w * k3 * q[p];
+        const double gsym = fma(k2w[cl], q[p] * q[p], k1w[cl]);
+        const double gasy = k3w[cl] * q[p];
         outg[2 * p + 1] = fma(omw, gg[2 * p + 1], gsym + gasy);
         outg[2 * p + 2] = fma(omw, gg[2 * p + 2], gsym - gasy);
     }
