@@ -241,6 +241,12 @@ __global__ void __launch_bounds__(128, (sizeof(T) == 4 ? 4 : 2))
             if (dup) v += Lin[q * S + idx + dup];
             return v;
         };
+        // f-phase populations and adjoints: start their trip from HBM into L2 now
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(A + i * S + idx + o.src(i)));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(Lin + i * S + idx));
+        }
         // ---- phase 1: g -- gather, moments, recovery, g part of dL/dtau and of the adjoint
         unsigned bounced = 0u;
         T h[19];

@@ -187,7 +187,7 @@ rlb_status rlb_create(const rlb_params* p, void* stream, void* workspace, size_t
         const char* t = getenv("RLB_TMA");
         g.tma = (t && t[0] == '1') ? 1 : 0;
         const char* v = getenv("RLB_F32_VARIANT");
-        g.variant = v ? atoi(v) : 0;
+        g.variant = v ? atoi(v) : 1;
     }
     Phys& ph = c->ph;
     ph.tau = p->tau;
