@@ -25,6 +25,9 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # results do not depend on launch variant or register allocation.
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC", "-Xcompiler",
               "-fvisibility=hidden", "--expt-relaxed-constexpr"]
+# The adjoint kernels run in one launch configuration, so contraction there
+# cannot make results depend on the launch; it is allowed for speed.
+FMAD_SOURCES = {"rlb_adjoint.cu"}
 
 
 def _nvcc() -> str:
@@ -41,7 +44,7 @@ def _digest() -> str:
             h.update(fh.read())
     with open(os.path.join(INCLUDE, "rlb.h"), "rb") as fh:
         h.update(fh.read())
-    h.update(" ".join(ARCH + NVCC_FLAGS).encode())
+    h.update(" ".join(ARCH + NVCC_FLAGS + sorted(FMAD_SOURCES)).encode())
     return h.hexdigest()[:12]
 
 
@@ -61,7 +64,10 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
 
     def compile_one(src):
         obj = os.path.join(BUILD, f"{os.path.splitext(src)[0]}_{tag}.o")
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra, "-I", INCLUDE, "-c", os.path.join(CSRC, src), "-o", obj]
+        flags = list(NVCC_FLAGS)
+        if src in FMAD_SOURCES:
+            flags[flags.index("-fmad=false")] = "-fmad=true"
+        cmd = [nvcc, *ARCH, *flags, *extra, "-I", INCLUDE, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

@@ -138,16 +138,21 @@ __device__ __forceinline__ void block_reduce4(double v0, double v1, double v2, d
     }
 }
 
-// Sum the per-block partials in block order and add them to the accumulators.
-__global__ void k_finalize(const double* __restrict__ red, int nblocks, double* dtau, double* dbeta_in) {
-    __shared__ double sm[4][32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;  // 128 threads: warp k reduces component k
-    double t = 0.0;
-    for (int b = lane; b < nblocks; b += 32) t += red[b * 4 + warp];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
-    if (lane == 0) sm[warp][0] = t;
+// Sum the per-block partials and add them to the accumulators.  256 threads
+// per component; thread t sums blocks t, t+256, ... in order, then a fixed
+// tree combines the 256 sums: the result does not depend on scheduling.
+__global__ void __launch_bounds__(1024) k_finalize(const double* __restrict__ red, int nblocks, double* dtau,
+                                                   double* dbeta_in) {
+    __shared__ double sm[4][256];
+    const int k = threadIdx.x >> 8, t = threadIdx.x & 255;
+    double acc = 0.0;
+    for (int b = t; b < nblocks; b += 256) acc += red[b * 4 + k];
+    sm[k][t] = acc;
     __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (t < h) sm[k][t] += sm[k][t + h];
+        __syncthreads();
+    }
     if (threadIdx.x == 0) {
         if (dtau) *dtau += sm[0][0];
         if (dbeta_in) {
@@ -192,12 +197,14 @@ struct AdjConst {
 };
 
 template <typename T, int XBC>
-__global__ void __launch_bounds__(128, (sizeof(T) == 4 ? 4 : 2))
+__global__ void __launch_bounds__(128, (sizeof(T) == 4 ? 5 : 2))
     k_adjoint_step(const T* __restrict__ A, const T* __restrict__ Lin, T* __restrict__ Lout, Geom g, Phys ph,
                    AdjConst<T> c, double* red) {
     const long long S = g.S;
     double tau_acc = 0.0, bin0 = 0.0, bin1 = 0.0, bin2 = 0.0;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < g.N; idx += gridDim.x * blockDim.x) {
+    // one cell per thread; the loop body runs at most once ('continue' skips to
+    // the block reduction, which every thread of the block reaches)
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < g.N; idx = g.N) {
         int x, y, z;
         cell_coords(g, idx, x, y, z);
         const bool ghost = (XBC != XBC_PERIODIC) && (x == 0 || x == g.nx - 1);
@@ -451,7 +458,7 @@ __global__ void __launch_bounds__(128) k_adjoint_fields(const double* __restrict
                                                         Phys ph, double* red) {
     const long long S = g.S;
     double bin0 = 0.0, bin1 = 0.0, bin2 = 0.0;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < g.N; idx += gridDim.x * blockDim.x) {
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < g.N; idx = g.N) {
         const int x = idx % g.nx;
         double lf[19], lg[19];
         double an = 0, ae = 0, ax = 0, ay = 0, az = 0;
@@ -485,10 +492,7 @@ __global__ void __launch_bounds__(128) k_adjoint_fields(const double* __restrict
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
-static inline int adj_blocks(int N) {
-    const int need = (N + 127) / 128;
-    return need < kAdjBlocksMax ? need : kAdjBlocksMax;
-}
+static inline int adj_blocks(int N) { return (N + 127) / 128; }
 
 cudaError_t launch_adjoint_macro(int prec, const Geom& g, const Phys& ph, const void* A, const double* dn,
                                  const double* deps, const double* dbeta, void* lam, cudaStream_t st) {
@@ -530,7 +534,7 @@ cudaError_t launch_adjoint_step(int prec, const Geom& g, const Phys& ph, const v
         adjoint_step_t<double>(g, ph, (const double*)A, (const double*)lam_in, (double*)lam_out, red, nb, st);
     else
         adjoint_step_t<float>(g, ph, (const float*)A, (const float*)lam_in, (float*)lam_out, red, nb, st);
-    k_finalize<<<1, 128, 0, st>>>(red, nb, dtau, dbeta_in);
+    k_finalize<<<1, 1024, 0, st>>>(red, nb, dtau, dbeta_in);
     return cudaGetLastError();
 }
 
@@ -545,7 +549,7 @@ cudaError_t launch_adjoint_fields(int prec, const Geom& g, const Phys& ph, const
     else
         k_adjoint_fields<float><<<nb, 128, 0, st>>>(n0, eps0, beta0, (const float*)A0, (const float*)lam0, dn0, deps0,
                                                     dbeta0, g, ph, red);
-    k_finalize<<<1, 128, 0, st>>>(red, nb, nullptr, dbeta_in);
+    k_finalize<<<1, 1024, 0, st>>>(red, nb, nullptr, dbeta_in);
     return cudaGetLastError();
 }
 

@@ -102,14 +102,16 @@ void layout(const rlb_params* p, long long* S, int* elem, size_t* state_bytes) {
 }
 
 size_t counters_bytes() { return align_up(sizeof(unsigned long long) * (2 * kCounterSlots + 3), kAlign); }
-size_t red_bytes() { return align_up(sizeof(double) * 4 * kAdjBlocksMax, kAlign); }
+size_t red_bytes(const rlb_params* p) {
+    return align_up(sizeof(double) * adj_red_doubles((long long)p->nx * p->ny * p->nz), kAlign);
+}
 
 size_t workspace_size(const rlb_params* p) {
     long long S;
     int elem;
     size_t sb;
     layout(p, &S, &elem, &sb);
-    return 2 * align_up(sb, kAlign) + counters_bytes() + red_bytes();
+    return 2 * align_up(sb, kAlign) + counters_bytes() + red_bytes(p);
 }
 
 rlb_status reset_counters(rlb_ctx* c) {

@@ -129,13 +129,12 @@ __global__ void __launch_bounds__(128) k_step_f64(const double* __restrict__ A, 
     for (int p = 0; p < 9; ++p) {
         const int cl = p < 3 ? 0 : 1;
         const double fsym = cl == 0 ? fs1 : fs2;
-        const double fasy = (cl == 0 ? fa1 : fa2) * q[p];
-        outf[2 * p + 1] = fma(omw, f[2 * p + 1], fsym + fasy);
-        outf[2 * p + 2] = fma(omw, f[2 * p + 2], fsym - fasy);
+        const double fa = cl == 0 ? fa1 : fa2;
+        outf[2 * p + 1] = fma(omw, f[2 * p + 1], fma(fa, q[p], fsym));
+        outf[2 * p + 2] = fma(omw, f[2 * p + 2], fma(-fa, q[p], fsym));
         const double gsym = fma(k2w[cl], q[p] * q[p], k1w[cl]);
-        const double gasy = k3w[cl] * q[p];
-        outg[2 * p + 1] = fma(omw, gg[2 * p + 1], gsym + gasy);
-        outg[2 * p + 2] = fma(omw, gg[2 * p + 2], gsym - gasy);
+        outg[2 * p + 1] = fma(omw, gg[2 * p + 1], fma(k3w[cl], q[p], gsym));
+        outg[2 * p + 2] = fma(omw, gg[2 * p + 2], fma(-k3w[cl], q[p], gsym));
     }
 #pragma unroll
     for (int i = 0; i < 19; ++i) {

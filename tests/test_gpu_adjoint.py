@@ -1,0 +1,285 @@
+"""Parity of the CUDA adjoint (through the C ABI) with the oracle's taped
+discrete adjoint, and of the autograd gradients with central finite
+differences (h = 1e-6, FP64) on the shock-tube and sphere workloads."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+from tests._helpers import tiny_workload
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    dict(nx=5, ny=4, nz=3, xbc=0, solid=()),
+    dict(nx=6, ny=5, nz=4, xbc=0, solid=((3, 2, 2),)),
+    dict(nx=9, ny=5, nz=4, xbc=1, solid=((4, 2, 1), (5, 2, 1))),
+    dict(nx=8, ny=1, nz=1, xbc=2, solid=()),
+    dict(nx=37, ny=9, nz=5, xbc=1, solid=((12, 4, 2), (13, 4, 2), (12, 5, 2))),
+]
+IDS = ["periodic", "solid", "inflow", "outflow2", "ragged"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+
+
+def _setup(case, prec, seed):
+    """A near-equilibrium state given to both sides: the GPU state in its own
+    layout (FP64 values or FP32 deviations), the oracle state in FP64 at the
+    very same point."""
+    from paper_0912_2913_gb300 import RLB
+
+    w = tiny_workload(case["nx"], case["ny"], case["nz"], case["xbc"], seed=seed, solid_cells=case["solid"])
+    p = oracle.Params(**w.params())
+    rng = np.random.default_rng(seed)
+    st = oracle.init(p, w.n, w.eps, w.beta, w.solid)
+    st *= 1.0 + 1e-3 * rng.uniform(-1, 1, size=st.shape)
+    sim = RLB.from_workload(w, prec, device="cuda:0").init_fields(w.n, w.eps, w.beta, w.solid)
+    fluid = np.ones((w.nz, w.ny, w.nx), bool) if w.solid is None else w.solid == 0
+    cells = sim.state_to_cells(sim.state()).cpu().numpy()  # solid markers included
+    if prec == "fp64":
+        cells[fluid] = st[fluid]
+    else:
+        fr, gr = oracle.equilibrium(sim.params.n_ref, sim.params.eps_ref, np.zeros(3), w.c_l)
+        ref = np.stack([fr, gr])
+        dev = (st - ref).astype(np.float32)
+        cells[fluid] = dev[fluid]
+        st = np.where(fluid[..., None, None], ref + dev.astype(np.float64), st)
+    gstate = sim.cells_to_state(torch.from_numpy(cells).cuda())
+    return w, p, sim, st, gstate, rng
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+TOL = {"fp64": 1e-11, "fp32": 1e-4}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_adjoint_step_parity(case, prec):
+    w, p, sim, st, gstate, rng = _setup(case, prec, 11)
+    lam_in = rng.normal(size=st.shape)
+    if prec == "fp32":
+        lam_in = lam_in.astype(np.float32).astype(np.float64)
+    ref_out, ref_dtau, ref_db = oracle.adjoint_step(p, st, lam_in, w.solid)
+    li = sim.cells_to_state(torch.from_numpy(lam_in).cuda())
+    lo = torch.full_like(li, float("nan"))
+    acc = torch.zeros(4, dtype=torch.float64, device="cuda")
+    sim.adjoint_step(gstate, li, lo, acc[0:1], acc[1:4])
+    got = sim.state_to_cells(lo).double().cpu().numpy()
+    assert not np.isnan(got).any()  # every element of lambda_t is written
+    assert _rel(got, ref_out) <= TOL[prec]
+    a = acc.cpu().numpy()
+    assert abs(a[0] - ref_dtau) <= TOL[prec] * max(abs(ref_dtau), 1e-12) * 10
+    if case["xbc"] == 1:
+        assert np.max(np.abs(a[1:] - ref_db)) <= TOL[prec] * max(np.max(np.abs(ref_db)), 1e-12) * 10
+    else:
+        assert np.all(a[1:] == 0.0)
+    sim.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", CASES[:3], ids=IDS[:3])
+def test_adjoint_macro_and_fields_parity(case, prec):
+    w, p, sim, st, gstate, rng = _setup(case, prec, 12)
+    shp = (w.nz, w.ny, w.nx)
+    dn, de, db = rng.normal(size=shp), rng.normal(size=shp), rng.normal(size=(3,) + shp)
+    if w.solid is not None:
+        m = w.solid.astype(bool)
+        dn[m] = de[m] = 0.0
+        db[:, m] = 0.0
+    ref = oracle.adjoint_macro(p, st, dn, de, db, w.solid)
+    lam = sim.new_state()
+    cu = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    sim.adjoint_macro(gstate, cu(dn), cu(de), cu(db), lam)
+    got = sim.state_to_cells(lam).double().cpu().numpy()
+    assert _rel(got, ref) <= TOL[prec]
+    # fields: lambda_0 random, derivative of the equilibrium initialisation
+    lam0 = rng.normal(size=st.shape)
+    if prec == "fp32":
+        lam0 = lam0.astype(np.float32).astype(np.float64)
+    rdn, rde, rdb, rdbi = oracle.adjoint_fields(p, w.n, w.eps, w.beta, lam0, w.solid)
+    acc = torch.zeros(3, dtype=torch.float64, device="cuda")
+    dn0, de0, db0 = torch.empty(shp, dtype=torch.float64, device="cuda"), torch.empty(
+        shp, dtype=torch.float64, device="cuda"), torch.empty((3,) + shp, dtype=torch.float64, device="cuda")
+    sim.adjoint_fields(cu(w.n), cu(w.eps), cu(w.beta), sim.cells_to_state(cu(lam0)), dn0, de0, db0, acc)
+    tol = 1e-12 if prec == "fp64" else 1e-6
+    for g_, r_ in ((dn0, rdn), (de0, rde), (db0, rdb)):
+        assert _rel(g_.cpu().numpy(), r_) <= tol
+    if case["xbc"] == 1:
+        assert np.max(np.abs(acc.cpu().numpy() - rdbi)) <= tol * np.max(np.abs(rdbi)) * 10
+    sim.close()
+
+
+def _oracle_grad(w, T, target, tau=None, beta_in=None):
+    """Oracle taped gradient of L = sum over interior non-solid cells (eps_T - target)^2."""
+    pd = w.params()
+    if tau is not None:
+        pd["tau"] = tau
+    if beta_in is not None:
+        pd["beta_in"] = beta_in
+    p = oracle.Params(**pd)
+    a = oracle.init(p, w.n, w.eps, w.beta, w.solid)
+    tape = [a.copy()]
+    for t in range(T):
+        a = oracle.step(p, a, w.solid, step_index=t)
+        tape.append(a)
+    n, e, b, _ = oracle.macro(p, a, w.solid)
+    m = _loss_mask(w)
+    r = np.where(m, e - target, 0.0)
+    lam = oracle.adjoint_macro(p, a, np.zeros_like(e), 2 * r, np.zeros_like(b), w.solid)
+    dtau, dbin = 0.0, np.zeros(3)
+    for t in range(T - 1, -1, -1):
+        lam, dt, db = oracle.adjoint_step(p, tape[t], lam, w.solid)
+        dtau += dt
+        dbin += db
+    dn, de, db0, dbi = oracle.adjoint_fields(p, w.n, w.eps, w.beta, lam, w.solid)
+    return float(np.sum(r * r)), dtau, dbin + dbi, de
+
+
+def _loss_mask(w):
+    m = np.ones((w.nz, w.ny, w.nx), bool)
+    if w.xbc != 0:
+        m[..., 0] = m[..., -1] = False
+    if w.solid is not None:
+        m &= w.solid == 0
+    return m
+
+
+def _gpu_loss_and_grad(w, T, target, prec, K=None, tau=None, beta_in=None, grad=True):
+    from paper_0912_2913_gb300 import RunSpec, rlb_run
+
+    spec = RunSpec.from_workload(w, prec, steps=T, checkpoint_every=K)
+    dev = "cuda:0"
+    tau_t = torch.tensor(w.tau if tau is None else tau, dtype=torch.float64, device=dev, requires_grad=grad)
+    bi = torch.tensor(w.beta_in if beta_in is None else beta_in, dtype=torch.float64, device=dev,
+                      requires_grad=grad)
+    n0 = torch.from_numpy(np.ascontiguousarray(w.n)).to(dev).requires_grad_(grad)
+    e0 = torch.from_numpy(np.ascontiguousarray(w.eps)).to(dev).requires_grad_(grad)
+    b0 = torch.from_numpy(np.ascontiguousarray(w.beta)).to(dev).requires_grad_(grad)
+    n, e, b = rlb_run(tau_t, bi, n0, e0, b0, spec)
+    m = torch.from_numpy(_loss_mask(w)).to(dev)
+    tg = torch.from_numpy(np.ascontiguousarray(target)).to(dev)
+    r = torch.where(m, e - tg, torch.zeros_like(e))
+    L = (r * r).sum()
+    if not grad:
+        return float(L)
+    L.backward()
+    return float(L), float(tau_t.grad), bi.grad.cpu().numpy(), e0.grad.cpu().numpy(), n0.grad, b0.grad
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("xbc", [2, 1])
+def test_autograd_matches_oracle_taped_gradient(xbc, prec):
+    nx, T = 14, 12
+    w = tiny_workload(nx, 3, 2, xbc, seed=21)
+    w.tau = 0.9
+    target = np.full((w.nz, w.ny, w.nx), 0.9)
+    L0, dtau0, dbin0, de0 = _oracle_grad(w, T, target)
+    L, dtau, dbin, de, _, _ = _gpu_loss_and_grad(w, T, target, prec, K=4)
+    tol = 1e-9 if prec == "fp64" else 2e-3
+    assert abs(L - L0) <= tol * abs(L0)
+    assert abs(dtau - dtau0) <= tol * abs(dtau0)
+    assert np.max(np.abs(de - de0)) <= tol * np.max(np.abs(de0))
+    if xbc == 1:
+        assert np.max(np.abs(dbin - dbin0)) <= tol * np.max(np.abs(dbin0))
+
+
+def test_shock_tube_gradient_vs_finite_differences():
+    """The adjoint 1D shock tube: 1600 cells with a seeded +-5% perturbation of
+    eps0, loss = L2 mismatch of eps at step 2000 against the unperturbed run at
+    tau = 0.85, checkpoints every 45 steps; gradient w.r.t. tau and eps0 vs
+    central differences of the FP64 GPU forward (h = 1e-6): 1e-5 relative."""
+    T = 2000
+    w = W.perturbed_shock_tube(steps=T)
+    tgt_w = W.shock_tube_1d(tau=0.85, steps=T)
+    from paper_0912_2913_gb300 import RLB
+
+    sim = RLB.from_workload(tgt_w, "fp64", device="cuda:0").init_fields(tgt_w.n, tgt_w.eps, tgt_w.beta).step(T)
+    target = sim.macro(where="host")[1]
+    sim.close()
+    L, dtau, _, de, _, _ = _gpu_loss_and_grad(w, T, target, "fp64", K=45)
+    h = 1e-6
+    Lp = _gpu_loss_and_grad(w, T, target, "fp64", tau=w.tau + h, grad=False)
+    Lm = _gpu_loss_and_grad(w, T, target, "fp64", tau=w.tau - h, grad=False)
+    fd = (Lp - Lm) / (2 * h)
+    assert abs(dtau - fd) <= 1e-5 * abs(fd), (dtau, fd)
+    rng = np.random.default_rng(16)
+    for j in rng.choice(np.arange(1, w.nx - 1), size=6, replace=False):
+        e_p, e_m = w.eps.copy(), w.eps.copy()
+        e_p[0, 0, j] += h
+        e_m[0, 0, j] -= h
+        wp = W.Workload(**{**w.__dict__, "eps": e_p})
+        wm = W.Workload(**{**w.__dict__, "eps": e_m})
+        fdj = (_gpu_loss_and_grad(wp, T, target, "fp64", grad=False) -
+               _gpu_loss_and_grad(wm, T, target, "fp64", grad=False)) / (2 * h)
+        assert abs(de[0, 0, j] - fdj) <= 1e-5 * abs(fdj) + 1e-7 * np.max(np.abs(de)), (j, de[0, 0, j], fdj)
+    # a seeded random direction in eps0
+    v = rng.uniform(-1, 1, size=w.eps.shape)
+    v[..., 0] = v[..., -1] = 0.0
+    wp = W.Workload(**{**w.__dict__, "eps": w.eps + h * v})
+    wm = W.Workload(**{**w.__dict__, "eps": w.eps - h * v})
+    fdv = (_gpu_loss_and_grad(wp, T, target, "fp64", grad=False) -
+           _gpu_loss_and_grad(wm, T, target, "fp64", grad=False)) / (2 * h)
+    assert abs(np.sum(de * v) - fdv) <= 1e-5 * abs(fdv)
+    # FP32 gradient against the FP64 one
+    L32, dtau32, _, de32, _, _ = _gpu_loss_and_grad(w, T, target, "fp32", K=45)
+    assert abs(dtau32 - dtau) <= 1e-3 * abs(dtau)
+    assert np.max(np.abs(de32 - de)) <= 1e-3 * np.max(np.abs(de))
+
+
+def test_oracle_taped_gradient_shock_tube_short():
+    """The same 1D problem over 200 steps: GPU FP64 gradient (sqrt(T)
+    checkpointing) against the oracle's taped adjoint."""
+    T = 200
+    w = W.perturbed_shock_tube(steps=T)
+    target = np.full((1, 1, w.nx), 0.5)
+    L0, dtau0, _, de0 = _oracle_grad(w, T, target)
+    L, dtau, _, de, _, _ = _gpu_loss_and_grad(w, T, target, "fp64")
+    assert abs(dtau - dtau0) <= 1e-9 * abs(dtau0)
+    assert np.max(np.abs(de - de0)) <= 1e-9 * np.max(np.abs(de0))
+
+
+def test_sphere_gradient_beta_in_and_tau():
+    """The adjoint 3D sphere (reduced to 60x30x30, 300 steps): loss on the
+    pressure P = eps/3 of the plane x = 36 against a run with inflow beta_x =
+    0.45; d/d beta_in_x and d/d tau of the FP64 adjoint vs central
+    differences (1e-5), FP32 adjoint vs FP64 adjoint (1e-3)."""
+    T = 300
+    w = W.sphere_3d(nx=60, ny=30, nz=30, steps=T)
+    tgt = W.sphere_3d(nx=60, ny=30, nz=30, steps=T, beta_in=0.45)
+    from paper_0912_2913_gb300 import RLB, RunSpec, rlb_run
+
+    sim = RLB.from_workload(tgt, "fp64", device="cuda:0").init_fields(tgt.n, tgt.eps, tgt.beta, tgt.solid).step(T)
+    P_t = torch.from_numpy(sim.macro(where="host")[1][:, :, 36] / 3.0).cuda()
+    sim.close()
+
+    def run(prec, tau, bx, grad=True):
+        spec = RunSpec.from_workload(w, prec, steps=T)
+        t = torch.tensor(tau, dtype=torch.float64, device="cuda", requires_grad=grad)
+        bi = torch.tensor([bx, 0.0, 0.0], dtype=torch.float64, device="cuda", requires_grad=grad)
+        f = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        n, e, b = rlb_run(t, bi, f(w.n), f(w.eps), f(w.beta), spec)
+        L = ((e[:, :, 36] / 3.0 - P_t) ** 2).sum()
+        if not grad:
+            return float(L)
+        L.backward()
+        return float(L), float(t.grad), float(bi.grad[0])
+
+    L, dtau, dbx = run("fp64", w.tau, 0.5)
+    h = 1e-6
+    fd_tau = (run("fp64", w.tau + h, 0.5, False) - run("fp64", w.tau - h, 0.5, False)) / (2 * h)
+    fd_bx = (run("fp64", w.tau, 0.5 + h, False) - run("fp64", w.tau, 0.5 - h, False)) / (2 * h)
+    assert abs(dtau - fd_tau) <= 1e-5 * abs(fd_tau), (dtau, fd_tau)
+    assert abs(dbx - fd_bx) <= 1e-5 * abs(fd_bx), (dbx, fd_bx)
+    L32, dtau32, dbx32 = run("fp32", w.tau, 0.5)
+    assert abs(dtau32 - dtau) <= 1e-3 * abs(dtau)
+    assert abs(dbx32 - dbx) <= 1e-3 * abs(dbx)
