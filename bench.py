@@ -37,6 +37,12 @@ if ROOT not in sys.path:
 METRIC = "MLUPS and % of HBM roofline, FP32 vs FP64, forward and adjoint step, 1 GB300"
 FALLBACK_HBM_GBS = 6800.0
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (vector and tensor), nominal
+# FP64 pipe work of one update of the all-FP64 step (57 moment additions,
+# ~28 recovery operations with IEEE sqrt and divisions counted at their
+# measured cost, ~125 equilibrium + BGK operations) and the measured DFMA rate
+# of the GB300 FP64 pipe (python -m paper_0912_2913_gb300.probes.run).
+FP64_OPS_PER_UPDATE = 210
+FP64_MEASURED_GOPS = 500.0
 
 # Algorithmic bytes per lattice update (every population read once and written once).
 BYTES_FWD = {"fp64": 38 * 8 * 2, "fp32": 38 * 4 * 2}
@@ -277,18 +283,39 @@ def e2e_run(w, job_steps, jobs, device):
             "job": f"{jobs} x (host fields -> init -> {job_steps} FP32 steps -> macro to host)"}
 
 
-def traffic_from_profiles(kernel: str, digest: str):
+def traffic_from_profiles(kernel: str, digest: str, workload: str):
     """DRAM bytes per launch from a committed ncu summary, if taken on this build."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
             d = json.load(fh)
-        e = d.get(kernel)
+        e = d.get(f"{kernel}/{workload}")
         if e and e.get("build") == digest:
             return float(e["dram_bytes_per_launch"])
     except Exception:
         pass
     return None
+
+
+def _leg(w, ms_total, steps, bytes_per_update, peak, extra=None):
+    ms = ms_total / steps
+    gbs = bytes_per_update * w.N / (ms * 1e-3) / 1e9
+    d = {"mlups": w.N / (ms * 1e-3) / 1e6, "ms_per_step": ms, "bytes_per_update": bytes_per_update,
+         "achieved_gbs": gbs, "frac_hbm": gbs / peak}
+    if extra:
+        d.update(extra)
+    return d
+
+
+def make_workload(name, steps):
+    import workloads as W
+
+    if name == "box512":
+        return W.random_box(L=512, steps=steps), ("random_box 512^3 periodic, eps = 1 + 0.2 phi (Gaussian random "
+                                                  "field, sigma 8), n = eps^(3/4), div-free beta, max|beta| = 0.3, "
+                                                  "tau = 0.7")
+    return W.sphere_3d(steps=steps), ("sphere_3d 200x100x100, inflow beta_x = 0.5, eps = n = 1; interior at rest, "
+                                      "eps = 1, n = 0.3; solid sphere r = 15 at (60,50,50); tau = 0.8")
 
 
 def run_ours(args):
@@ -298,60 +325,53 @@ def run_ours(args):
     device = torch.device("cuda", local)
     torch.cuda.set_device(device)
     init_dist(ws, "nccl")
-    import workloads as W
     from paper_0912_2913_gb300 import RLB
     from paper_0912_2913_gb300 import build as B
 
-    w = W.sphere_3d(steps=args.steps)
+    w, wdesc = make_workload(args.workload, args.steps)
     peak, peak_kind = measured_peaks()
     legs = {}
     with ClockSampler(local) as clk:
-        # headline leg: FP32 forward
+        # headline leg: FP32 deviation storage, forward
         sim = RLB.from_workload(w, "fp32", device=device).init_fields(w.n, w.eps, w.beta, w.solid)
         ms, launches = time_forward(sim, args.steps, args.warmup, ws, device)
         ms_max = max_over_ranks(ms, ws, device)
         value = aggregate(w.N, args.steps, ms_max, ws)
         stats32 = sim.stats()
-        sim.close()
-        per_launch_ms = ms / max(launches, 1)
-        achieved = BYTES_FWD["fp32"] * w.N / (per_launch_ms * 1e-3) / 1e9
-        legs["fp32_forward"] = {"mlups": w.N * args.steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / args.steps,
-                                "bytes_per_update": BYTES_FWD["fp32"], "achieved_gbs": achieved,
-                                "frac_hbm": achieved / peak}
+        legs["fp32_forward"] = _leg(w, ms, args.steps, BYTES_FWD["fp32"], peak)
+        achieved = legs["fp32_forward"]["achieved_gbs"] * args.steps / max(launches, 1)
         if not args.headline_only:
+            ka = max(1, args.steps // 4)
+            if not args.no_adjoint:
+                ms_all, ms_k, _ = time_adjoint(sim, ka, 3)
+                legs["fp32_adjoint"] = _leg(w, ms_all, ka, BYTES_ADJ["fp32"] + BYTES_FWD["fp32"], peak,
+                                            {"adjoint_kernel_ms": ms_k / ka,
+                                             "ratio_to_forward": (ms_all / ka) / (ms / args.steps)})
+            sim.close()
+            del sim
+            torch.cuda.empty_cache()
             sim = RLB.from_workload(w, "fp64", device=device).init_fields(w.n, w.eps, w.beta, w.solid)
             k64 = max(1, args.steps // 4)
             ms64, _ = time_forward(sim, k64, max(3, args.warmup // 4), 1, device)
-            a64 = BYTES_FWD["fp64"] * w.N / (ms64 / k64 * 1e-3) / 1e9
-            legs["fp64_forward"] = {"mlups": w.N * k64 / (ms64 * 1e-3) / 1e6, "ms_per_step": ms64 / k64,
-                                    "bytes_per_update": BYTES_FWD["fp64"], "achieved_gbs": a64,
-                                    "frac_hbm": a64 / peak}
-            ka = max(1, k64 // 2)
-            ms_all, ms_k, _ = time_adjoint(sim, ka, 3)
-            legs["fp64_adjoint"] = {"mlups": w.N * ka / (ms_all * 1e-3) / 1e6, "ms_per_step": ms_all / ka,
-                                    "adjoint_kernel_ms": ms_k / ka,
-                                    "ratio_to_forward": (ms_all / ka) / (ms64 / k64),
-                                    "bytes_per_update": BYTES_ADJ["fp64"] + BYTES_FWD["fp64"],
-                                    "frac_hbm": (BYTES_ADJ["fp64"] + BYTES_FWD["fp64"]) * w.N /
-                                    (ms_all / ka * 1e-3) / 1e9 / peak}
-            sim.close()
-            sim = RLB.from_workload(w, "fp32", device=device).init_fields(w.n, w.eps, w.beta, w.solid)
-            sim.step(50)
-            ka = max(1, args.steps // 4)
-            ms_all, ms_k, _ = time_adjoint(sim, ka, 3)
-            legs["fp32_adjoint"] = {"mlups": w.N * ka / (ms_all * 1e-3) / 1e6, "ms_per_step": ms_all / ka,
-                                    "adjoint_kernel_ms": ms_k / ka,
-                                    "ratio_to_forward": (ms_all / ka) / (ms / args.steps),
-                                    "bytes_per_update": BYTES_ADJ["fp32"] + BYTES_FWD["fp32"],
-                                    "frac_hbm": (BYTES_ADJ["fp32"] + BYTES_FWD["fp32"]) * w.N /
-                                    (ms_all / ka * 1e-3) / 1e9 / peak}
-            sim.close()
+            legs["fp64_forward"] = _leg(w, ms64, k64, BYTES_FWD["fp64"], peak,
+                                        {"bound": "alu", "fp64_ops_per_update": FP64_OPS_PER_UPDATE,
+                                         "fp64_alu_frac": FP64_OPS_PER_UPDATE * w.N / (ms64 / k64 * 1e-3) /
+                                         (FP64_MEASURED_GOPS * 1e9)})
+            if not args.no_adjoint:
+                ka = max(1, k64 // 2)
+                ms_all, ms_k, _ = time_adjoint(sim, ka, 3)
+                legs["fp64_adjoint"] = _leg(w, ms_all, ka, BYTES_ADJ["fp64"] + BYTES_FWD["fp64"], peak,
+                                            {"adjoint_kernel_ms": ms_k / ka,
+                                             "ratio_to_forward": (ms_all / ka) / (ms64 / k64)})
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
     clocks = clk.summary()
     e2e = None
     if rank == 0 and not args.no_e2e:
         e2e = e2e_run(w, args.e2e_steps, 1, device)
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.workload == "sphere":
         cpu = cpu_baseline(w, args.cpu_budget)
     if rank == 0:
         kern = "k_step_f32"
@@ -359,13 +379,12 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "sphere_3d 200x100x100, inflow beta_x=0.5, eps 1/0.1, n 1/0.3, sphere r=15 at "
-                                   "(60,50,50), tau=0.8, FP32 deviation storage (FP64 recovery)",
-                       "cells": w.N, "l2": "state 608 MB > L2 (no flush needed)",
+            "config": {"workload": wdesc + "; FP32 deviation storage, FP64 recovery root", "cells": w.N,
+                       "l2": "state larger than L2 (no flush needed)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
-                         "traffic": traffic_from_profiles(kern, B._digest()), "kernel": kern,
+                         "traffic": traffic_from_profiles(kern, B._digest(), args.workload), "kernel": kern,
                          "bytes_per_launch": BYTES_FWD["fp32"] * w.N},
             "legs": legs,
             "clocks": clocks,
@@ -414,6 +433,29 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_profile(args):
+    """Short runs of the benchmark workload for ncu captures: --profile step
+    runs warm-up + --steps forward steps; --profile adjoint runs --steps
+    (forward recompute + adjoint) steps; --profile box runs forward steps of
+    the periodic random box of side --box."""
+    import torch
+
+    import workloads as W
+    from paper_0912_2913_gb300 import RLB
+
+    w = W.random_box(L=args.box, steps=args.steps) if args.profile == "box" else W.sphere_3d(steps=args.steps)
+    sim = RLB.from_workload(w, args.precision, device="cuda:0").init_fields(w.n, w.eps, w.beta, w.solid)
+    if args.profile in ("step", "box"):
+        sim.step(args.steps)
+    else:
+        sim.step(5)
+        time_adjoint(sim, args.steps, 1)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": args.profile, "precision": args.precision, "steps": args.steps,
+                      "stats": sim.stats()}), flush=True)
+    sim.close()
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -425,7 +467,16 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--headline-only", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--workload", choices=["sphere", "box512"], default="sphere")
+    ap.add_argument("--profile", choices=["step", "adjoint", "box"], default=None,
+                    help="short run of one kernel family for ncu captures (no JSON bench line)")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--box", type=int, default=256)
     args = ap.parse_args(argv)
+    if args.profile:
+        run_profile(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
