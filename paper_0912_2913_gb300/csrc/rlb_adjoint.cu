@@ -113,6 +113,41 @@ __device__ __forceinline__ void recovery_adjoint(T a_eps, T abx, T aby, T abz, T
     vz = 3 * abz * rD + c * Mz;
 }
 
+// Warp partial sums written to red[(global warp)*4 + k], no block barrier:
+// tau in binary32 across the warp for the FP32 path (the per-cell terms are
+// binary32 already), the beta_in terms only when a lane has one.
+template <typename T>
+__device__ __forceinline__ void warp_partials(double tau, double b0, double b1, double b2, double* red) {
+    const unsigned full = 0xffffffffu;
+    double v0;
+    if constexpr (sizeof(T) == 4) {
+        float t = (float)tau;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(full, t, off);
+        v0 = (double)t;
+    } else {
+        v0 = tau;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v0 += __shfl_xor_sync(full, v0, off);
+    }
+    double v1 = b0, v2 = b1, v3 = b2;
+    if (__any_sync(full, b0 != 0.0 || b1 != 0.0 || b2 != 0.0)) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            v1 += __shfl_xor_sync(full, v1, off);
+            v2 += __shfl_xor_sync(full, v2, off);
+            v3 += __shfl_xor_sync(full, v3, off);
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+        const long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+        red[wg * 4 + 0] = v0;
+        red[wg * 4 + 1] = v1;
+        red[wg * 4 + 2] = v2;
+        red[wg * 4 + 3] = v3;
+    }
+}
+
 // Block reduction of four doubles into red[blockIdx.x*4 + k].
 __device__ __forceinline__ void block_reduce4(double v0, double v1, double v2, double v3, double* red) {
     __shared__ double sm[4][32];
@@ -355,7 +390,7 @@ __global__ void __launch_bounds__(128, (sizeof(T) == 4 ? 5 : 2))
                 tacc += muf[2 * p + 1] * (h[2 * p + 1] - (fs + fz)) + muf[2 * p + 2] * (h[2 * p + 2] - (fs - fz));
             }
         }
-        tau_acc += (double)tacc * c.inv_tau2;
+        tau_acc += (sizeof(T) == 4) ? (double)(tacc * (T)c.inv_tau2) : (double)tacc * c.inv_tau2;
         T aS, fbx, fby, fbz;
         f_eq_adjoint_S<T>(muf, Sfull, bx, by, bz, c.inv_cl, aS, fbx, fby, fbz);
         T vE, vx, vy, vz;
@@ -393,7 +428,7 @@ __global__ void __launch_bounds__(128, (sizeof(T) == 4 ? 5 : 2))
             }
         }
     }
-    block_reduce4(tau_acc, bin0, bin1, bin2, red);
+    warp_partials<T>(tau_acc, bin0, bin1, bin2, red);
 }
 
 // ---------------------------------------------------------------------------
@@ -493,6 +528,7 @@ __global__ void __launch_bounds__(128) k_adjoint_fields(const double* __restrict
 // Launchers
 // ---------------------------------------------------------------------------
 static inline int adj_blocks(int N) { return (N + 127) / 128; }
+static inline int adj_warps(int N) { return 4 * adj_blocks(N); }
 
 cudaError_t launch_adjoint_macro(int prec, const Geom& g, const Phys& ph, const void* A, const double* dn,
                                  const double* deps, const double* dbeta, void* lam, cudaStream_t st) {
@@ -534,7 +570,7 @@ cudaError_t launch_adjoint_step(int prec, const Geom& g, const Phys& ph, const v
         adjoint_step_t<double>(g, ph, (const double*)A, (const double*)lam_in, (double*)lam_out, red, nb, st);
     else
         adjoint_step_t<float>(g, ph, (const float*)A, (const float*)lam_in, (float*)lam_out, red, nb, st);
-    k_finalize<<<1, 1024, 0, st>>>(red, nb, dtau, dbeta_in);
+    k_finalize<<<1, 1024, 0, st>>>(red, adj_warps(g.N), dtau, dbeta_in);
     return cudaGetLastError();
 }
 

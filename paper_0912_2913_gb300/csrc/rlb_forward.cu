@@ -97,13 +97,28 @@ __global__ void __launch_bounds__(128) k_step_f64(const double* __restrict__ A, 
     my *= ph.c_l;
     mz *= ph.c_l;
     // Recovery with eps = 3P: eps = -E + sqrt(4E^2 - 3M^2), beta = 3M/(3E + eps).
+    // Square root and reciprocals from binary32 seeds (converted on the integer
+    // pipe) with two FP64 Newton corrections each: full double accuracy at a
+    // fraction of the IEEE sequences' cost on this GPU's FP64 pipe.
     const double m2 = fma(mx, mx, fma(my, my, mz * mz));
     const double disc = fma(4.0 * E, E, -3.0 * m2);
-    const double eps = sqrt(disc) - E;
-    const double r3 = 3.0 / fma(3.0, E, eps);
+    const float ys = rsqrtf(d2f_seed(disc));
+    const double hs = f2d(0.5f * ys);
+    double sq = disc * f2d(ys);
+    sq = fma(fma(-sq, sq, disc), hs, sq);
+    sq = fma(fma(-sq, sq, disc), hs, sq);
+    const double eps = sq - E;
+    const double D = fma(3.0, E, eps);
+    double rD = f2d(__frcp_rn(d2f_seed(D)));
+    rD = fma(rD, fma(-D, rD, 1.0), rD);
+    rD = fma(rD, fma(-D, rD, 1.0), rD);
+    const double r3 = 3.0 * rD;
     const double bx = mx * r3, by = my * r3, bz = mz * r3;
     const double b2 = fma(bx, bx, fma(by, by, bz * bz));
-    const double gam2 = 1.0 / (1.0 - b2);
+    const double omb2 = 1.0 - b2;
+    double gam2 = f2d(__frcp_rn(d2f_seed(omb2)));
+    gam2 = fma(gam2, fma(-omb2, gam2, 1.0), gam2);
+    gam2 = fma(gam2, fma(-omb2, gam2, 1.0), gam2);
     const bool unphys = !(pos_finite(sf) && pos_finite(E) && nonneg_finite(disc) && pos_finite(eps) && below_one(b2));
     const bool nonpos = nonpositive_eq((float)bx, (float)by, (float)bz, (float)ph.c_l);
 

@@ -68,8 +68,8 @@ cudaError_t launch_conversions(const float* fi, const double* di, long long n, d
 cudaError_t launch_check_solid_planes(const Geom& g, const uint8_t* solid, unsigned long long* flag,
                                       cudaStream_t stream);
 
-// Adjoint.  'red' holds 4 doubles of partial sums per 128-cell block.
-inline long long adj_red_doubles(long long N) { return 4 * ((N + 127) / 128); }
+// Adjoint.  'red' holds 4 doubles of partial sums per 32-cell warp.
+inline long long adj_red_doubles(long long N) { return 4 * 4 * ((N + 127) / 128); }
 cudaError_t launch_adjoint_macro(int prec, const Geom& g, const Phys& ph, const void* A, const double* dn,
                                  const double* deps, const double* dbeta, void* lam, cudaStream_t stream);
 cudaError_t launch_adjoint_step(int prec, const Geom& g, const Phys& ph, const void* A, const void* lam_in,

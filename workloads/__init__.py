@@ -24,8 +24,9 @@ Workloads (the paper's, plus the synthetic stand-ins the benchmarks use):
   c_l = 1 and at the first step for c_l >= 2.
 * ``random_box``      -- a periodic box with eps = 1 + 0.2 phi, phi a
   Gaussian random field filtered with a Gaussian of sigma = 8 cells and
-  normalised to unit standard deviation, n = eps^(3/4), and beta the curl of
-  a three-component field filtered the same way, scaled to max |beta| = 0.3.
+  normalised to max |phi| = 1 (a unit standard deviation reaches phi < -5 at
+  512^3, eps < 0), n = eps^(3/4), and beta the curl of a three-component
+  field filtered the same way, scaled to max |beta| = 0.3.
 * ``perturbed_shock_tube`` -- the shock tube with eps multiplied by
   (1 + 0.05 U(-1, 1)) from seed 5 (gradient studies).
 """
@@ -133,7 +134,8 @@ def random_box(L: int = 512, tau: float = 0.7, steps: int = 1000, sigma: float =
     (phi_hat,), _ = _filtered_noise(shape, sigma, np.random.default_rng(seeds[0]), 1)
     phi = np.fft.irfftn(phi_hat, s=shape, axes=(0, 1, 2))
     del phi_hat
-    phi = (phi - phi.mean()) / phi.std()
+    phi = phi - phi.mean()
+    phi /= np.abs(phi).max()
     eps = 1.0 + amp * phi
     del phi
     if not np.all(eps > 0):
