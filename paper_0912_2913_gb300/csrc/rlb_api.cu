@@ -183,6 +183,8 @@ rlb_status rlb_create(const rlb_params* p, void* stream, void* workspace, size_t
     g.N = p->nx * p->ny * p->nz;
     g.S = S;
     g.xbc = p->xbc;
+    g.div_nx = make_fast_div((unsigned)g.nx);
+    g.div_ny = make_fast_div((unsigned)g.ny);
     {
         // Tuning knobs (no effect on results): RLB_TMA=1 selects the TMA-staged
         // FP32 step, RLB_F32_VARIANT the launch variant of the plain one.
@@ -190,6 +192,8 @@ rlb_status rlb_create(const rlb_params* p, void* stream, void* workspace, size_t
         g.tma = (t && t[0] == '1') ? 1 : 0;
         const char* v = getenv("RLB_F32_VARIANT");
         g.variant = v ? atoi(v) : 1;
+        const char* pb = getenv("RLB_PIPE_BLOCKS");
+        g.pipe_blocks = pb ? atoi(pb) : 3;
     }
     Phys& ph = c->ph;
     ph.tau = p->tau;

@@ -19,15 +19,36 @@
 
 namespace rlb {
 
-// fetch(q, i): pulled population of plane q (velocity i = q mod 19), with
-// bounce-back already applied; put(q, v): store the post-collision value.
-template <class Fetch, class Put>
-__device__ __forceinline__ void collide_cell_f32(Fetch fetch, Put put, const Dev32& c, bool& unphys, bool& nonpos) {
+// fetch(q, i): the population of plane q (velocity i = q mod 19) pulled from
+// x - e_i, as stored (a solid neighbour yields the solid marker);
+// bounce(q, i): the cell's own population of the opposite velocity, the link
+// bounce-back value; put(q, v): store the post-collision value.
+// A pulled marker is a NaN, so the sum of a phase's 19 values is NaN exactly
+// when a marker (or a non-finite population) is among them: the per-value
+// marker tests run only then.
+template <bool SOLID, class Fetch, class Bounce>
+__device__ __forceinline__ void gather_phase(float* v, int base, Fetch fetch, Bounce bounce) {
+#pragma unroll
+    for (int i = 0; i < 19; ++i) v[i] = fetch(base + i, i);
+    if (SOLID) {
+        float s = v[0];
+#pragma unroll
+        for (int i = 1; i < 19; ++i) s += v[i];
+        if (isnan(s)) {
+#pragma unroll
+            for (int i = 1; i < 19; ++i)
+                if (is_solid(v[i])) v[i] = bounce(base + i, i);
+        }
+    }
+}
+
+template <bool SOLID, class Fetch, class Bounce, class Put>
+__device__ __forceinline__ void collide_cell_f32(Fetch fetch, Bounce bounce, Put put, const Dev32& c, bool& unphys,
+                                                 bool& nonpos) {
     const float om = c.omega;
     // ---- phase 1: energy-momentum populations g_i (they alone fix eps, beta) ----
     float gg[19];
-#pragma unroll
-    for (int i = 0; i < 19; ++i) gg[i] = fetch(19 + i, i);
+    gather_phase<SOLID>(gg, 19, fetch, bounce);
     float dE = gg[0], d[9];
 #pragma unroll
     for (int p = 0; p < 9; ++p) {
@@ -76,8 +97,7 @@ __device__ __forceinline__ void collide_cell_f32(Fetch fetch, Put put, const Dev
     }
     // ---- phase 2: number populations f_i ----
     float f[19];
-#pragma unroll
-    for (int i = 0; i < 19; ++i) f[i] = fetch(i, i);
+    gather_phase<SOLID>(f, 0, fetch, bounce);
     float dS = f[0];
 #pragma unroll
     for (int i = 1; i < 19; ++i) dS += f[i];

@@ -137,10 +137,15 @@ struct PullOffsets {
     }
 };
 
+// Cell coordinates by multiply-high division with host-computed magic
+// numbers (division by an invariant integer, Granlund and Montgomery 1994).
+__device__ __forceinline__ unsigned fast_div(unsigned n, const FastDiv& d) {
+    return (__umulhi(n, d.mul) + n) >> d.shift;
+}
 __device__ __forceinline__ void cell_coords(const Geom& g, int idx, int& x, int& y, int& z) {
-    const int yz = idx / g.nx;
+    const int yz = (int)fast_div((unsigned)idx, g.div_nx);
     x = idx - yz * g.nx;
-    z = yz / g.ny;
+    z = (int)fast_div((unsigned)yz, g.div_ny);
     y = yz - z * g.ny;
 }
 

@@ -227,14 +227,71 @@ __global__ void __launch_bounds__(256, MINB) k_step_f32(const float* __restrict_
 #pragma unroll
         for (int i = 0; i < 19; ++i) asm volatile("prefetch.global.L2 [%0];" ::"l"(A + i * S + idx + o.src(i)));
     }
-    auto fetch = [&](int q, int i) {
-        float v = __ldg(A + q * S + idx + o.src(i));
-        if (SOLID && i > 0 && is_solid(v)) v = __ldg(A + (q - i + opp(i)) * S + idx);  // link bounce-back
-        return v;
-    };
+    auto fetch = [&](int q, int i) { return __ldg(A + q * S + idx + o.src(i)); };
+    auto bounce = [&](int q, int i) { return __ldg(A + (q - i + opp(i)) * S + idx); };  // link bounce-back
     bool unphys, nonpos;
-    collide_cell_f32(fetch, put, c, unphys, nonpos);
+    collide_cell_f32<SOLID>(fetch, bounce, put, c, unphys, nonpos);
     if (count) count_flags(cnt, unphys, nonpos, (unsigned long long)step_index * (unsigned long long)g.N + idx);
+}
+
+// Persistent variant: a grid of (SMs x resident blocks) threads walks the
+// lattice with a grid stride; before colliding its current cell a thread
+// issues L2 prefetches for all 38 populations of its next cell, so every
+// gather hits L2 while HBM streams the next cells in (software pipelining
+// without registers).  Same per-cell arithmetic as k_step_f32.
+template <int XBC, bool SOLID, bool CS>
+__global__ void __launch_bounds__(256, 3) k_step_f32_pipe(const float* __restrict__ A, float* __restrict__ B, Geom g,
+                                                          Dev32 c, Counters cnt, int count, long long step_index) {
+    const long long S = g.S;
+    const int stride = gridDim.x * blockDim.x;
+    auto prefetch_cell = [&](int idx) {
+        int x, y, z;
+        cell_coords(g, idx, x, y, z);
+        if (XBC != XBC_PERIODIC && (x == 0 || x == g.nx - 1)) return;
+        const PullOffsets o(g, x, y, z);
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(A + (19 + i) * S + idx + o.src(i)));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(A + i * S + idx + o.src(i)));
+        }
+    };
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < g.N) prefetch_cell(idx);
+    for (; idx < g.N; idx += stride) {
+        if (idx + stride < g.N) prefetch_cell(idx + stride);
+        int x, y, z;
+        cell_coords(g, idx, x, y, z);
+        if (XBC != XBC_PERIODIC && (x == 0 || x == g.nx - 1)) {
+            if (XBC == XBC_INFLOW_OUTFLOW && x == 0) {
+#pragma unroll
+                for (int q = 0; q < 38; ++q) B[q * S + idx] = __ldg(A + q * S + idx);
+            }
+            continue;
+        }
+        const PullOffsets o(g, x, y, z);
+        const int dup = (XBC != XBC_PERIODIC && x == g.nx - 2) ? 1 : ((XBC == XBC_OUTFLOW_BOTH && x == 1) ? -1 : 0);
+        float* Bc = B + idx;
+        auto put = [&](int q, float v) {
+            if (CS) {
+                __stcs(Bc + q * S, v);
+                if (dup) __stcs(Bc + q * S + dup, v);
+            } else {
+                Bc[q * S] = v;
+                if (dup) Bc[q * S + dup] = v;
+            }
+        };
+        if (SOLID && is_solid(__ldg(A + 19 * S + idx))) {
+            const float m = solid_marker_f();
+#pragma unroll
+            for (int q = 0; q < 38; ++q) Bc[q * S] = m;
+            continue;
+        }
+        auto fetch = [&](int q, int i) { return __ldg(A + q * S + idx + o.src(i)); };
+        auto bounce = [&](int q, int i) { return __ldg(A + (q - i + opp(i)) * S + idx); };
+        bool unphys, nonpos;
+        collide_cell_f32<SOLID>(fetch, bounce, put, c, unphys, nonpos);
+        if (count) count_flags(cnt, unphys, nonpos, (unsigned long long)step_index * (unsigned long long)g.N + idx);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -427,6 +484,22 @@ static void launch_step_t(int prec, const Geom& g, const Phys& ph, const void* A
             case 1: k_step_f32<XBC, SOLID, 3, true><<<nb, 256, 0, st>>>((const float*)A, (float*)B, g, c, cnt, cs, step_index); break;
             case 2: k_step_f32<XBC, SOLID, 4, false><<<nb, 256, 0, st>>>((const float*)A, (float*)B, g, c, cnt, cs, step_index); break;
             case 3: k_step_f32<XBC, SOLID, 4, true><<<nb, 256, 0, st>>>((const float*)A, (float*)B, g, c, cnt, cs, step_index); break;
+            case 4:
+            case 5: {
+                static int nsm = 0;
+                if (nsm == 0) {
+                    int dev = 0;
+                    cudaGetDevice(&dev);
+                    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+                }
+                unsigned grid = (unsigned)nsm * (unsigned)(g.pipe_blocks > 0 ? g.pipe_blocks : 3);
+                if (grid > nb) grid = nb;
+                if (g.variant == 4)
+                    k_step_f32_pipe<XBC, SOLID, false><<<grid, 256, 0, st>>>((const float*)A, (float*)B, g, c, cnt, cs, step_index);
+                else
+                    k_step_f32_pipe<XBC, SOLID, true><<<grid, 256, 0, st>>>((const float*)A, (float*)B, g, c, cnt, cs, step_index);
+                break;
+            }
             default: k_step_f32<XBC, SOLID, 3, true><<<nb, 256, 0, st>>>((const float*)A, (float*)B, g, c, cnt, cs, step_index); break;
         }
     }

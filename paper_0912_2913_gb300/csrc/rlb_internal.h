@@ -15,6 +15,17 @@ enum : int { XBC_PERIODIC = 0, XBC_INFLOW_OUTFLOW = 1, XBC_OUTFLOW_BOTH = 2 };
 // Number of counter slots that warps spread their statistics over.
 constexpr int kCounterSlots = 4096;
 
+// n / d = (umulhi(n, mul) + n) >> shift for 0 <= n < 2^31, 1 <= d < 2^31.
+struct FastDiv {
+    unsigned mul, shift;
+};
+inline FastDiv make_fast_div(unsigned d) {
+    unsigned l = 0;
+    while (l < 32 && (1ull << l) < d) ++l;  // l = ceil(log2 d)
+    const unsigned long long m = ((1ull << 32) * ((1ull << l) - d)) / d + 1;
+    return FastDiv{(unsigned)m, l};
+}
+
 // Lattice geometry.  Populations of plane q (0..37) of a state start at
 // element q * S; cell index c = (z*ny + y)*nx + x.
 struct Geom {
@@ -25,6 +36,8 @@ struct Geom {
     int xbc;
     int tma;     // 1: use the TMA-staged FP32 step where the lattice allows it
     int variant; // launch variant of the one-cell-per-thread FP32 step (tuning)
+    int pipe_blocks;  // resident blocks per SM of the persistent variant (tuning)
+    FastDiv div_nx, div_ny;
 };
 
 // Physical parameters, with the derived constants the kernels use.

@@ -128,10 +128,9 @@ __global__ void __launch_bounds__(256, MINB)
             const float* row = st + r * nx;
             auto fetch = [&](int q, int i) {
                 const int ex = vel_x(i);
-                float v = row[q * plane_elems + (ex > 0 ? xm : (ex < 0 ? xp : x))];
-                if (SOLID && i > 0 && is_solid(v)) v = __ldg(A + (q - i + opp(i)) * S + idx);  // link bounce-back
-                return v;
+                return row[q * plane_elems + (ex > 0 ? xm : (ex < 0 ? xp : x))];
             };
+            auto bounce = [&](int q, int i) { return __ldg(A + (q - i + opp(i)) * S + idx); };  // link bounce-back
             const int dup = (XBC != XBC_PERIODIC && x == nx - 2) ? 1 : ((XBC == XBC_OUTFLOW_BOTH && x == 1) ? -1 : 0);
             float* Bc = B + idx;
             auto put = [&](int q, float v) {
@@ -139,7 +138,7 @@ __global__ void __launch_bounds__(256, MINB)
                 if (dup) Bc[q * S + dup] = v;
             };
             bool unphys, nonpos;
-            collide_cell_f32(fetch, put, c, unphys, nonpos);
+            collide_cell_f32<SOLID>(fetch, bounce, put, c, unphys, nonpos);
             if (count) count_flags(cnt, unphys, nonpos, (unsigned long long)step_index * (unsigned long long)g.N + idx);
         }
         __syncthreads();  // every thread is done reading stage s
