@@ -118,7 +118,10 @@ RLB_API rlb_status rlb_init_fields(rlb_ctx* ctx, const double* n, const double* 
 /* Enqueue nsteps time steps of Eqs. (lbe1), (lbe2) on the context's state
  * (fused pull streaming with link bounce-back, moments, eps = 3P recovery,
  * equilibria Eqs. (equil1s, equil2as, equil2bs), BGK relaxation, boundary
- * planes).  Asynchronous.  nsteps >= 0.                                     */
+ * planes).  Asynchronous, except that the first call on an RLB_FP32_DEV
+ * context times its launch variants (bit-identical results) on the
+ * context's second buffer and synchronises once; make that first call
+ * before any stream capture.  nsteps >= 0.                                  */
 RLB_API rlb_status rlb_step(rlb_ctx* ctx, int32_t nsteps);
 
 /* One time step from the device state src into the device state dst (both

@@ -294,11 +294,20 @@ __global__ void __launch_bounds__(128, (sizeof(T) == 4 ? 5 : 2))
         T h[19];
 #pragma unroll
         for (int i = 0; i < 19; ++i) h[i] = A[(19 + i) * S + idx + o.src(i)];
+        {
+            // a pulled solid marker is a NaN: test the per-value markers only
+            // when the sum of the gathered values is NaN
+            T sum = h[0];
 #pragma unroll
-        for (int i = 1; i < 19; ++i) {
-            if (is_solid(h[i])) {
-                bounced |= 1u << i;
-                h[i] = A[(19 + opp(i)) * S + idx];
+            for (int i = 1; i < 19; ++i) sum += h[i];
+            if (isnan(sum)) {
+#pragma unroll
+                for (int i = 1; i < 19; ++i) {
+                    if (is_solid(h[i])) {
+                        bounced |= 1u << i;
+                        h[i] = A[(19 + opp(i)) * S + idx];
+                    }
+                }
             }
         }
         T dE = h[0], dd[9];

@@ -191,7 +191,7 @@ rlb_status rlb_create(const rlb_params* p, void* stream, void* workspace, size_t
         const char* t = getenv("RLB_TMA");
         g.tma = (t && t[0] == '1') ? 1 : 0;
         const char* v = getenv("RLB_F32_VARIANT");
-        g.variant = v ? atoi(v) : 1;
+        g.variant = v ? atoi(v) : -1;  // -1: chosen by timing at the first step
         const char* pb = getenv("RLB_PIPE_BLOCKS");
         g.pipe_blocks = pb ? atoi(pb) : 3;
     }
@@ -304,10 +304,58 @@ rlb_status rlb_init_fields(rlb_ctx* c, const double* n, const double* eps, const
     return RLB_OK;
 }
 
+// Launch variants of the FP32 step compute bit-identical results; which one
+// is fastest depends on the lattice (measured: the 64-register one on the
+// 200x100x100 sphere, the 80-register one with L2 prefetch on a 512^3 box).
+// The first FP32 rlb_step times both on the context's second buffer (which
+// the step then overwrites) and keeps the faster.  This first call
+// synchronises the stream once.
+static rlb_status autotune_f32(rlb_ctx* c) {
+    const int cand[2] = {1, 2};
+    float best = 1e30f;
+    int pick = 1;
+    cudaEvent_t e0, e1;
+    RLB_CUDA(c, cudaEventCreate(&e0), "event");
+    RLB_CUDA(c, cudaEventCreate(&e1), "event");
+    for (int k = 0; k < 2; ++k) {
+        c->g.variant = cand[k];
+        cudaError_t e = launch_step(c->p.prec, c->g, c->ph, c->A, c->B, c->cnt, false, 0, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+        for (int r = 0; r < 3 && e == cudaSuccess; ++r)
+            e = launch_step(c->p.prec, c->g, c->ph, c->A, c->B, c->cnt, false, 0, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return cuda_fail(c, e, "autotune");
+        }
+        c->launches += 4;
+        if (ms < best) {
+            best = ms;
+            pick = cand[k];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->g.variant = pick;
+    return RLB_OK;
+}
+
 rlb_status rlb_step(rlb_ctx* c, int32_t nsteps) {
     RLB_LATCHED(c);
     if (nsteps < 0) return fail(c, RLB_ERR_ARG, "nsteps must be >= 0");
     if (!c->inited) return fail(c, RLB_ERR_STATE, "rlb_step before rlb_init_fields");
+    if (c->g.variant < 0 && nsteps > 0) {
+        if (c->p.prec == RLB_FP32_DEV && !c->g.tma) {
+            rlb_status s = autotune_f32(c);
+            if (s != RLB_OK) return s;
+        } else {
+            c->g.variant = 1;
+        }
+    }
     for (int32_t t = 0; t < nsteps; ++t) {
         rlb_status s = after_launch(c, launch_step(c->p.prec, c->g, c->ph, c->A, c->B, c->cnt, true, c->steps, c->stream),
                                     "step");
@@ -323,6 +371,7 @@ rlb_status rlb_step(rlb_ctx* c, int32_t nsteps) {
 rlb_status rlb_step_into(rlb_ctx* c, const void* src, void* dst) {
     RLB_LATCHED(c);
     if (!src || !dst || src == dst) return fail(c, RLB_ERR_ARG, "src and dst must be distinct device buffers");
+    if (c->g.variant < 0) c->g.variant = 1;
     return after_launch(c, launch_step(c->p.prec, c->g, c->ph, src, dst, c->cnt, false, 0, c->stream), "step_into");
 }
 
