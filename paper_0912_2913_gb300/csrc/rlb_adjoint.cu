@@ -234,7 +234,7 @@ struct AdjConst {
 template <typename T, int XBC>
 __global__ void __launch_bounds__(128, (sizeof(T) == 4 ? 5 : 2))
     k_adjoint_step(const T* __restrict__ A, const T* __restrict__ Lin, T* __restrict__ Lout, Geom g, Phys ph,
-                   AdjConst<T> c, double* red) {
+                   AdjConst<T> c, double* red, const double* __restrict__ inflow_d) {
     const long long S = g.S;
     double tau_acc = 0.0, bin0 = 0.0, bin1 = 0.0, bin2 = 0.0;
     // one cell per thread; the loop body runs at most once ('continue' skips to
@@ -255,18 +255,19 @@ __global__ void __launch_bounds__(128, (sizeof(T) == 4 ? 5 : 2))
                 }
             }
             if (XBC == XBC_INFLOW_OUTFLOW && x == 0 && !is_solid(A[idx])) {
-                double lf[19], lg[19];
-#pragma unroll
-                for (int i = 0; i < 19; ++i) {
-                    lf[i] = (double)Lin[i * S + idx];
-                    lg[i] = (double)Lin[(19 + i) * S + idx];
+                // the inflow plane holds eq(n_in, eps_in, beta_in): its adjoint
+                // adds lambda_{t+1} . d eq_in / d beta_in (a per-context table)
+                T a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll 2
+                for (int q = 0; q < 38; ++q) {
+                    const T l = Lin[q * S + idx];
+                    a0 += l * (T)inflow_d[3 * q + 0];
+                    a1 += l * (T)inflow_d[3 * q + 1];
+                    a2 += l * (T)inflow_d[3 * q + 2];
                 }
-                double an, ae, ax, ay, az;
-                eq_fields_adjoint(lf, lg, ph.n_in, ph.eps_in, ph.beta_in[0], ph.beta_in[1], ph.beta_in[2], ph, an,
-                                  ae, ax, ay, az);
-                bin0 += ax;
-                bin1 += ay;
-                bin2 += az;
+                bin0 += (double)a0;
+                bin1 += (double)a1;
+                bin2 += (double)a2;
             }
             continue;
         }
@@ -440,6 +441,27 @@ __global__ void __launch_bounds__(128, (sizeof(T) == 4 ? 5 : 2))
     warp_partials<T>(tau_acc, bin0, bin1, bin2, red);
 }
 
+// d eq_j(n_in, eps_in, beta_in) / d beta_in,a for the 38 populations (one
+// thread per population, FP64): the adjoint of the inflow plane.
+__global__ void k_inflow_derivs(Phys ph, double* out) {
+    const int j = threadIdx.x;
+    if (j >= 38) return;
+    double lf[19], lg[19];
+    for (int i = 0; i < 19; ++i) lf[i] = lg[i] = 0.0;
+    if (j < 19) lf[j] = 1.0; else lg[j - 19] = 1.0;
+    double an, ae, ax, ay, az;
+    eq_fields_adjoint(lf, lg, ph.n_in, ph.eps_in, ph.beta_in[0], ph.beta_in[1], ph.beta_in[2], ph, an, ae, ax, ay, az);
+    out[3 * j + 0] = ax;
+    out[3 * j + 1] = ay;
+    out[3 * j + 2] = az;
+}
+
+cudaError_t launch_inflow_derivs(const Phys& ph, double* out, cudaStream_t st) {
+    set_last_launch_count(1);
+    k_inflow_derivs<<<1, 64, 0, st>>>(ph, out);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Adjoint of the macroscopic output: n = S sqrt(1 - b2), eps, beta.
 // ---------------------------------------------------------------------------
@@ -552,7 +574,7 @@ cudaError_t launch_adjoint_macro(int prec, const Geom& g, const Phys& ph, const 
 
 template <typename T>
 static void adjoint_step_t(const Geom& g, const Phys& ph, const T* A, const T* Li, T* Lo, double* red, int nb,
-                           cudaStream_t st) {
+                           const double* inflow_d, cudaStream_t st) {
     AdjConst<T> c;
     c.om = (T)ph.omega;
     c.omw = (T)(1.0 - ph.omega);
@@ -565,20 +587,21 @@ static void adjoint_step_t(const Geom& g, const Phys& ph, const T* A, const T* L
     c.eps_ref = ph.eps_ref;
     c.inv_tau2 = ph.omega * ph.omega;
     switch (g.xbc) {
-        case XBC_PERIODIC: k_adjoint_step<T, XBC_PERIODIC><<<nb, 128, 0, st>>>(A, Li, Lo, g, ph, c, red); break;
-        case XBC_INFLOW_OUTFLOW: k_adjoint_step<T, XBC_INFLOW_OUTFLOW><<<nb, 128, 0, st>>>(A, Li, Lo, g, ph, c, red); break;
-        default: k_adjoint_step<T, XBC_OUTFLOW_BOTH><<<nb, 128, 0, st>>>(A, Li, Lo, g, ph, c, red); break;
+        case XBC_PERIODIC: k_adjoint_step<T, XBC_PERIODIC><<<nb, 128, 0, st>>>(A, Li, Lo, g, ph, c, red, inflow_d); break;
+        case XBC_INFLOW_OUTFLOW: k_adjoint_step<T, XBC_INFLOW_OUTFLOW><<<nb, 128, 0, st>>>(A, Li, Lo, g, ph, c, red, inflow_d); break;
+        default: k_adjoint_step<T, XBC_OUTFLOW_BOTH><<<nb, 128, 0, st>>>(A, Li, Lo, g, ph, c, red, inflow_d); break;
     }
 }
 
 cudaError_t launch_adjoint_step(int prec, const Geom& g, const Phys& ph, const void* A, const void* lam_in,
-                                void* lam_out, double* red, double* dtau, double* dbeta_in, cudaStream_t st) {
+                                void* lam_out, double* red, const double* inflow_d, double* dtau, double* dbeta_in,
+                                cudaStream_t st) {
     const int nb = adj_blocks(g.N);
     set_last_launch_count(2);
     if (prec == 0)
-        adjoint_step_t<double>(g, ph, (const double*)A, (const double*)lam_in, (double*)lam_out, red, nb, st);
+        adjoint_step_t<double>(g, ph, (const double*)A, (const double*)lam_in, (double*)lam_out, red, nb, inflow_d, st);
     else
-        adjoint_step_t<float>(g, ph, (const float*)A, (const float*)lam_in, (float*)lam_out, red, nb, st);
+        adjoint_step_t<float>(g, ph, (const float*)A, (const float*)lam_in, (float*)lam_out, red, nb, inflow_d, st);
     k_finalize<<<1, 1024, 0, st>>>(red, adj_warps(g.N), dtau, dbeta_in);
     return cudaGetLastError();
 }

@@ -29,6 +29,7 @@ struct rlb_ctx {
     void* B;  // the other buffer
     Counters cnt;
     double* red;  // adjoint partial sums
+    double* inflow_d;  // d eq_in / d beta_in, 38 x 3
     size_t state_bytes;
     int elem;
     int64_t steps;
@@ -101,7 +102,9 @@ void layout(const rlb_params* p, long long* S, int* elem, size_t* state_bytes) {
     *state_bytes = (size_t)38 * (size_t)(*S) * (size_t)(*elem);
 }
 
-size_t counters_bytes() { return align_up(sizeof(unsigned long long) * (2 * kCounterSlots + 3), kAlign); }
+size_t counters_bytes() {
+    return align_up(sizeof(unsigned long long) * (2 * kCounterSlots + 3), kAlign) + align_up(sizeof(double) * 38 * 3, kAlign);
+}
 size_t red_bytes(const rlb_params* p) {
     return align_up(sizeof(double) * adj_red_doubles((long long)p->nx * p->ny * p->nz), kAlign);
 }
@@ -228,8 +231,10 @@ rlb_status rlb_create(const rlb_params* p, void* stream, void* workspace, size_t
     c->cnt.first_bad = c->cnt.slots + 2 * kCounterSlots;
     c->cnt.macro_bad = c->cnt.first_bad + 1;
     c->cnt.pipe_err = c->cnt.first_bad + 2;
+    c->inflow_d = (double*)(base + 2 * sb + align_up(sizeof(unsigned long long) * (2 * kCounterSlots + 3), kAlign));
     c->red = (double*)(base + 2 * sb + counters_bytes());
     s = reset_counters(c);
+    if (s == RLB_OK) s = after_launch(c, launch_inflow_derivs(c->ph, c->inflow_d, c->stream), "inflow table");
     if (s != RLB_OK) {
         rlb_destroy(c);
         return s;
@@ -474,8 +479,8 @@ rlb_status rlb_adjoint_step(rlb_ctx* c, const void* state_t, const void* lam_in,
     RLB_LATCHED(c);
     if (!state_t || !lam_in || !lam_out || lam_in == lam_out) return fail(c, RLB_ERR_ARG, "bad buffers");
     if (!dL_dtau_accum || !dL_dbeta_in_accum) return fail(c, RLB_ERR_ARG, "accumulators are required");
-    return after_launch(c, launch_adjoint_step(c->p.prec, c->g, c->ph, state_t, lam_in, lam_out, c->red, dL_dtau_accum,
-                                               dL_dbeta_in_accum, c->stream),
+    return after_launch(c, launch_adjoint_step(c->p.prec, c->g, c->ph, state_t, lam_in, lam_out, c->red, c->inflow_d,
+                                               dL_dtau_accum, dL_dbeta_in_accum, c->stream),
                         "adjoint_step");
 }
 

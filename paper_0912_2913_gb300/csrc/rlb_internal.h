@@ -86,7 +86,10 @@ inline long long adj_red_doubles(long long N) { return 4 * 4 * ((N + 127) / 128)
 cudaError_t launch_adjoint_macro(int prec, const Geom& g, const Phys& ph, const void* A, const double* dn,
                                  const double* deps, const double* dbeta, void* lam, cudaStream_t stream);
 cudaError_t launch_adjoint_step(int prec, const Geom& g, const Phys& ph, const void* A, const void* lam_in,
-                                void* lam_out, double* red, double* dtau, double* dbeta_in, cudaStream_t stream);
+                                void* lam_out, double* red, const double* inflow_d, double* dtau, double* dbeta_in,
+                                cudaStream_t stream);
+// d eq_in / d beta_in table (38 x 3 doubles) of the inflow state.
+cudaError_t launch_inflow_derivs(const Phys& ph, double* out, cudaStream_t stream);
 cudaError_t launch_adjoint_fields(int prec, const Geom& g, const Phys& ph, const double* n0, const double* eps0,
                                   const double* beta0, const void* A0, const void* lam0, double* dn0,
                                   double* deps0, double* dbeta0, double* red, double* dbeta_in,
