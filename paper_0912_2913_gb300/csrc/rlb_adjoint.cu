@@ -117,7 +117,7 @@ __device__ __forceinline__ void recovery_adjoint(T a_eps, T abx, T aby, T abz, T
 // tau in binary32 across the warp for the FP32 path (the per-cell terms are
 // binary32 already), the beta_in terms only when a lane has one.
 template <typename T>
-__device__ __forceinline__ void warp_partials(double tau, double b0, double b1, double b2, double* red) {
+__device__ __forceinline__ void warp_partials(double tau, double b0, double b1, double b2, bool has_b, double* red) {
     const unsigned full = 0xffffffffu;
     double v0;
     if constexpr (sizeof(T) == 4) {
@@ -131,7 +131,7 @@ __device__ __forceinline__ void warp_partials(double tau, double b0, double b1, 
         for (int off = 16; off > 0; off >>= 1) v0 += __shfl_xor_sync(full, v0, off);
     }
     double v1 = b0, v2 = b1, v3 = b2;
-    if (__any_sync(full, b0 != 0.0 || b1 != 0.0 || b2 != 0.0)) {
+    if (__any_sync(full, has_b)) {
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
             v1 += __shfl_xor_sync(full, v1, off);
@@ -231,15 +231,35 @@ struct AdjConst {
     double eps_ref, inv_tau2;
 };
 
-template <typename T, int XBC>
-__global__ void __launch_bounds__(128, (sizeof(T) == 4 ? 5 : 2))
+// PIPE: persistent grid-stride loop that prefetches the next cell's state
+// gather and adjoint inputs into L2 while the current cell is processed;
+// otherwise one cell per thread.
+template <typename T, int XBC, int MINB, bool PIPE>
+__global__ void __launch_bounds__(128, MINB)
     k_adjoint_step(const T* __restrict__ A, const T* __restrict__ Lin, T* __restrict__ Lout, Geom g, Phys ph,
                    AdjConst<T> c, double* red, const double* __restrict__ inflow_d) {
     const long long S = g.S;
     double tau_acc = 0.0, bin0 = 0.0, bin1 = 0.0, bin2 = 0.0;
-    // one cell per thread; the loop body runs at most once ('continue' skips to
-    // the block reduction, which every thread of the block reaches)
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < g.N; idx = g.N) {
+    bool has_b = false;
+    const int stride = PIPE ? gridDim.x * blockDim.x : g.N;
+    auto prefetch_cell = [&](int cidx) {
+        int x, y, z;
+        cell_coords(g, cidx, x, y, z);
+        if (XBC != XBC_PERIODIC && (x == 0 || x == g.nx - 1)) return;
+        const PullOffsets o(g, x, y, z);
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(A + (19 + i) * S + cidx + o.src(i)));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(A + i * S + cidx + o.src(i)));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(Lin + (19 + i) * S + cidx));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(Lin + i * S + cidx));
+        }
+    };
+    if (PIPE && blockIdx.x * blockDim.x + threadIdx.x < g.N) prefetch_cell(blockIdx.x * blockDim.x + threadIdx.x);
+    // the loop ends for every thread before the warp reduction ('continue'
+    // skips to the next cell)
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < g.N; idx += stride) {
+        if (PIPE && idx + stride < g.N) prefetch_cell(idx + stride);
         int x, y, z;
         cell_coords(g, idx, x, y, z);
         const bool ghost = (XBC != XBC_PERIODIC) && (x == 0 || x == g.nx - 1);
@@ -268,6 +288,7 @@ __global__ void __launch_bounds__(128, (sizeof(T) == 4 ? 5 : 2))
                 bin0 += (double)a0;
                 bin1 += (double)a1;
                 bin2 += (double)a2;
+                has_b = true;
             }
             continue;
         }
@@ -284,11 +305,13 @@ __global__ void __launch_bounds__(128, (sizeof(T) == 4 ? 5 : 2))
             if (dup) v += Lin[q * S + idx + dup];
             return v;
         };
-        // f-phase populations and adjoints: start their trip from HBM into L2 now
+        if (!PIPE) {
+            // f-phase populations and adjoints: start their trip from HBM into L2 now
 #pragma unroll
-        for (int i = 0; i < 19; ++i) {
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(A + i * S + idx + o.src(i)));
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(Lin + i * S + idx));
+            for (int i = 0; i < 19; ++i) {
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(A + i * S + idx + o.src(i)));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(Lin + i * S + idx));
+            }
         }
         // ---- phase 1: g -- gather, moments, recovery, g part of dL/dtau and of the adjoint
         unsigned bounced = 0u;
@@ -438,7 +461,7 @@ __global__ void __launch_bounds__(128, (sizeof(T) == 4 ? 5 : 2))
             }
         }
     }
-    warp_partials<T>(tau_acc, bin0, bin1, bin2, red);
+    warp_partials<T>(tau_acc, bin0, bin1, bin2, has_b, red);
 }
 
 // d eq_j(n_in, eps_in, beta_in) / d beta_in,a for the 38 populations (one
@@ -573,8 +596,8 @@ cudaError_t launch_adjoint_macro(int prec, const Geom& g, const Phys& ph, const 
 }
 
 template <typename T>
-static void adjoint_step_t(const Geom& g, const Phys& ph, const T* A, const T* Li, T* Lo, double* red, int nb,
-                           const double* inflow_d, cudaStream_t st) {
+static int adjoint_step_t(const Geom& g, const Phys& ph, const T* A, const T* Li, T* Lo, double* red, int nb,
+                          const double* inflow_d, cudaStream_t st) {
     AdjConst<T> c;
     c.om = (T)ph.omega;
     c.omw = (T)(1.0 - ph.omega);
@@ -586,11 +609,42 @@ static void adjoint_step_t(const Geom& g, const Phys& ph, const T* A, const T* L
     c.g0b = (T)(4.0 - 2.0 * ph.inv_cl2);
     c.eps_ref = ph.eps_ref;
     c.inv_tau2 = ph.omega * ph.omega;
-    switch (g.xbc) {
-        case XBC_PERIODIC: k_adjoint_step<T, XBC_PERIODIC><<<nb, 128, 0, st>>>(A, Li, Lo, g, ph, c, red, inflow_d); break;
-        case XBC_INFLOW_OUTFLOW: k_adjoint_step<T, XBC_INFLOW_OUTFLOW><<<nb, 128, 0, st>>>(A, Li, Lo, g, ph, c, red, inflow_d); break;
-        default: k_adjoint_step<T, XBC_OUTFLOW_BOTH><<<nb, 128, 0, st>>>(A, Li, Lo, g, ph, c, red, inflow_d); break;
+    auto go = [&](auto kern, bool pipe, int minb) {
+        int grid = nb;
+        if (pipe) {
+            static int nsm = 0;
+            if (nsm == 0) {
+                int dev = 0;
+                cudaGetDevice(&dev);
+                cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+            }
+            const int pg = nsm * minb;
+            grid = pg < nb ? pg : nb;
+        }
+        kern<<<grid, 128, 0, st>>>(A, Li, Lo, g, ph, c, red, inflow_d);
+        return grid;
+    };
+    int grid = nb;
+    if (sizeof(T) == 8) {
+        switch (g.xbc) {
+            case XBC_PERIODIC: grid = go(k_adjoint_step<T, XBC_PERIODIC, 2, false>, false, 2); break;
+            case XBC_INFLOW_OUTFLOW: grid = go(k_adjoint_step<T, XBC_INFLOW_OUTFLOW, 2, false>, false, 2); break;
+            default: grid = go(k_adjoint_step<T, XBC_OUTFLOW_BOTH, 2, false>, false, 2); break;
+        }
+    } else if (g.adj_pipe) {
+        switch (g.xbc) {
+            case XBC_PERIODIC: grid = go(k_adjoint_step<T, XBC_PERIODIC, 4, true>, true, 4); break;
+            case XBC_INFLOW_OUTFLOW: grid = go(k_adjoint_step<T, XBC_INFLOW_OUTFLOW, 4, true>, true, 4); break;
+            default: grid = go(k_adjoint_step<T, XBC_OUTFLOW_BOTH, 4, true>, true, 4); break;
+        }
+    } else {
+        switch (g.xbc) {
+            case XBC_PERIODIC: grid = go(k_adjoint_step<T, XBC_PERIODIC, 4, false>, false, 4); break;
+            case XBC_INFLOW_OUTFLOW: grid = go(k_adjoint_step<T, XBC_INFLOW_OUTFLOW, 4, false>, false, 4); break;
+            default: grid = go(k_adjoint_step<T, XBC_OUTFLOW_BOTH, 4, false>, false, 4); break;
+        }
     }
+    return grid;
 }
 
 cudaError_t launch_adjoint_step(int prec, const Geom& g, const Phys& ph, const void* A, const void* lam_in,
@@ -598,11 +652,14 @@ cudaError_t launch_adjoint_step(int prec, const Geom& g, const Phys& ph, const v
                                 cudaStream_t st) {
     const int nb = adj_blocks(g.N);
     set_last_launch_count(2);
+    int grid;
     if (prec == 0)
-        adjoint_step_t<double>(g, ph, (const double*)A, (const double*)lam_in, (double*)lam_out, red, nb, inflow_d, st);
+        grid = adjoint_step_t<double>(g, ph, (const double*)A, (const double*)lam_in, (double*)lam_out, red, nb,
+                                      inflow_d, st);
     else
-        adjoint_step_t<float>(g, ph, (const float*)A, (const float*)lam_in, (float*)lam_out, red, nb, inflow_d, st);
-    k_finalize<<<1, 1024, 0, st>>>(red, adj_warps(g.N), dtau, dbeta_in);
+        grid = adjoint_step_t<float>(g, ph, (const float*)A, (const float*)lam_in, (float*)lam_out, red, nb, inflow_d,
+                                     st);
+    k_finalize<<<1, 1024, 0, st>>>(red, grid * 4, dtau, dbeta_in);
     return cudaGetLastError();
 }
 

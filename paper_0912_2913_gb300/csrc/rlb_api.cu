@@ -195,6 +195,10 @@ rlb_status rlb_create(const rlb_params* p, void* stream, void* workspace, size_t
         g.tma = (t && t[0] == '1') ? 1 : 0;
         const char* v = getenv("RLB_F32_VARIANT");
         g.variant = v ? atoi(v) : -1;  // -1: chosen by timing at the first step
+        const char* am = getenv("RLB_ADJ_MINB");
+        g.adj_minb = am ? atoi(am) : 4;
+        const char* ap = getenv("RLB_ADJ_PIPE");
+        g.adj_pipe = ap ? atoi(ap) : 1;
         const char* pb = getenv("RLB_PIPE_BLOCKS");
         g.pipe_blocks = pb ? atoi(pb) : 3;
     }
