@@ -300,10 +300,15 @@ __global__ void __launch_bounds__(128, MINB)
         const PullOffsets o(g, x, y, z);
         // mu = lambda_{t+1}(x), plus the outflow ghost that copies x
         const int dup = (XBC != XBC_PERIODIC && x == g.nx - 2) ? 1 : ((XBC == XBC_OUTFLOW_BOTH && x == 1) ? -1 : 0);
-        auto load_mu = [&](int q) {
-            T v = Lin[q * S + idx];
-            if (dup) v += Lin[q * S + idx + dup];
-            return v;
+        // rare cases (a cell copied by an outflow ghost, links to solid cells)
+        // take branches, so the common cell runs straight-line loads/stores
+        auto load_mu = [&](T* mu, int base) {
+#pragma unroll
+            for (int i = 0; i < 19; ++i) mu[i] = Lin[(base + i) * S + idx];
+            if (dup) {
+#pragma unroll
+                for (int i = 0; i < 19; ++i) mu[i] += Lin[(base + i) * S + idx + dup];
+            }
         };
         if (!PIPE) {
             // f-phase populations and adjoints: start their trip from HBM into L2 now
@@ -383,49 +388,102 @@ __global__ void __launch_bounds__(128, MINB)
         }
         const T q[9] = {bx, by, bz, bx + by, bx - by, bx + bz, bx - bz, by + bz, by - bz};
         const T eg = epst * gam2;
+        // Everything the collision adjoint needs from mu reduces to a few
+        // weighted pair sums (sigma_p = mu_{+p} + mu_{-p}, delta_p = mu_{+p} -
+        // mu_{-p}, weight w_p, q_p = e_p . beta):
+        //   S1 = sum w sigma,  Sq2 = sum w sigma q^2,  Sdq = sum w delta q,
+        //   Vq = sum w sigma q e_p,  Vd = sum w delta e_p.
+        // With them (Eqs. equil2as/equil2bs and their derivatives):
+        //   sum mu_i geq_i = mu_0 geq_0 + k1 S1 + k2 Sq2 + k3 Sdq,
+        //   d/d eps = S1/c_l^2 + gamma^2 (SYM + ASY) + rest-particle term,
+        //   d/d gamma^2 = eps (SYM + ASY + rest term), d/d b2 = -2 eps gamma^2 (S1 + w0 mu_0)/c_l^2,
+        //   d/d beta = eps gamma^2 (12 Vq / c_l^2 + 4 Vd / c_l) + (chain through gamma^2 and b2) beta,
+        // SYM = (6 Sq2 - 2 b2 S1)/c_l^2, ASY = 4 Sdq / c_l; and likewise for f.
         T mug[19];
-#pragma unroll
-        for (int i = 0; i < 19; ++i) mug[i] = load_mu(19 + i);
-        T tacc;
+        load_mu(mug, 19);
+        T tacc;  // sum mu (h - eq), both sets
+        T ae, gbx, gby, gbz;
         {
-            // g^eq (as stored: values for FP64, deviations for FP32)
-            const T geq0 = (sizeof(T) == 8) ? (T)kW0 * (4 * eg - epst * (2 * c.inv_cl2 + 1) - 2 * eg * b2 * c.inv_cl2)
-                                            : (T)kW0 * (e0 * c.g0a + eg * b2 * c.g0b);
-            tacc = mug[0] * (h[0] - geq0);
-            const T k1 = (e0 - 2 * eg * b2) * c.inv_cl2, k2 = 6 * eg * c.inv_cl2, k3 = 4 * eg * c.inv_cl;
+            T muh = mug[0] * h[0];
+#pragma unroll
+            for (int i = 1; i < 19; ++i) muh += mug[i] * h[i];
+            T S1 = 0, Sq2 = 0, Sdq = 0, Vq[3] = {0, 0, 0}, Vd[3] = {0, 0, 0};
 #pragma unroll
             for (int p = 0; p < 9; ++p) {
                 const T w = (T)pair_w(p);
-                const T gs = w * (k2 * q[p] * q[p] + k1), ga = w * k3 * q[p];
-                tacc += mug[2 * p + 1] * (h[2 * p + 1] - (gs + ga)) + mug[2 * p + 2] * (h[2 * p + 2] - (gs - ga));
+                const T ws = w * (mug[2 * p + 1] + mug[2 * p + 2]);
+                const T wd = w * (mug[2 * p + 1] - mug[2 * p + 2]);
+                S1 += ws;
+                const T wsq = ws * q[p];
+                Sq2 += wsq * q[p];
+                Sdq += wd * q[p];
+                const int ex = pair_ex(p), ey = pair_ey(p), ez = pair_ez(p);
+                if (ex) { Vq[0] += wsq; Vd[0] += wd; }
+                if (ey > 0) { Vq[1] += wsq; Vd[1] += wd; }
+                if (ey < 0) { Vq[1] -= wsq; Vd[1] -= wd; }
+                if (ez > 0) { Vq[2] += wsq; Vd[2] += wd; }
+                if (ez < 0) { Vq[2] -= wsq; Vd[2] -= wd; }
             }
+            const T m0 = mug[0], w0 = (T)kW0;
+            const T k1 = (e0 - 2 * eg * b2) * c.inv_cl2, k2 = 6 * eg * c.inv_cl2, k3 = 4 * eg * c.inv_cl;
+            const T geq0 = (sizeof(T) == 8) ? w0 * (4 * eg - epst * (2 * c.inv_cl2 + 1) - 2 * eg * b2 * c.inv_cl2)
+                                            : w0 * (e0 * c.g0a + eg * b2 * c.g0b);
+            tacc = muh - (m0 * geq0 + k1 * S1 + k2 * Sq2 + k3 * Sdq);
+            const T SYM = (6 * Sq2 - 2 * b2 * S1) * c.inv_cl2;
+            const T ASY = 4 * c.inv_cl * Sdq;
+            ae = c.inv_cl2 * S1 + gam2 * (SYM + ASY) + w0 * m0 * (4 * gam2 - (2 * c.inv_cl2 + 1) - 2 * gam2 * b2 * c.inv_cl2);
+            const T gg2 = SYM + ASY + w0 * m0 * (4 - 2 * b2 * c.inv_cl2);
+            const T gb2 = -2 * gam2 * c.inv_cl2 * (S1 + w0 * m0);
+            const T rad = 2 * epst * (gb2 + gam2 * gam2 * gg2);
+            const T cq = eg * 12 * c.inv_cl2, cd = eg * 4 * c.inv_cl;
+            gbx = cq * Vq[0] + cd * Vd[0] + rad * bx;
+            gby = cq * Vq[1] + cd * Vd[1] + rad * by;
+            gbz = cq * Vq[2] + cd * Vd[2] + rad * bz;
         }
-        T ae, gbx, gby, gbz;
-        g_eq_adjoint<T>(mug, epst, bx, by, bz, b2, gam2, c.inv_cl, c.inv_cl2, ae, gbx, gby, gbz);
         // ---- phase 2: f -- gather, S, f part of dL/dtau and of the adjoint
 #pragma unroll
-        for (int i = 0; i < 19; ++i)
-            h[i] = (bounced >> i) & 1u ? A[opp(i) * S + idx] : A[i * S + idx + o.src(i)];
+        for (int i = 0; i < 19; ++i) h[i] = A[i * S + idx + o.src(i)];
+        if (bounced) {
+#pragma unroll
+            for (int i = 1; i < 19; ++i)
+                if ((bounced >> i) & 1u) h[i] = A[opp(i) * S + idx];
+        }
         T dS = h[0];
 #pragma unroll
         for (int i = 1; i < 19; ++i) dS += h[i];
         const T Sfull = (sizeof(T) == 8) ? dS : dS + c.n_ref;
         T muf[19];
-#pragma unroll
-        for (int i = 0; i < 19; ++i) muf[i] = load_mu(i);
+        load_mu(muf, 0);
+        T aS, fbx, fby, fbz;
         {
-            const T fa = 3 * Sfull * c.inv_cl;
-            tacc += muf[0] * (h[0] - (T)kW0 * dS);
+            T muh = muf[0] * h[0];
+#pragma unroll
+            for (int i = 1; i < 19; ++i) muh += muf[i] * h[i];
+            T F1 = 0, Fdq = 0, Vf[3] = {0, 0, 0};
 #pragma unroll
             for (int p = 0; p < 9; ++p) {
                 const T w = (T)pair_w(p);
-                const T fs = w * dS, fz = w * fa * q[p];
-                tacc += muf[2 * p + 1] * (h[2 * p + 1] - (fs + fz)) + muf[2 * p + 2] * (h[2 * p + 2] - (fs - fz));
+                const T ws = w * (muf[2 * p + 1] + muf[2 * p + 2]);
+                const T wd = w * (muf[2 * p + 1] - muf[2 * p + 2]);
+                F1 += ws;
+                Fdq += wd * q[p];
+                const int ex = pair_ex(p), ey = pair_ey(p), ez = pair_ez(p);
+                if (ex) Vf[0] += wd;
+                if (ey > 0) Vf[1] += wd;
+                if (ey < 0) Vf[1] -= wd;
+                if (ez > 0) Vf[2] += wd;
+                if (ez < 0) Vf[2] -= wd;
             }
+            const T w0 = (T)kW0;
+            const T fa = 3 * Sfull * c.inv_cl;
+            // f^eq_{+-p} = w_p (fb +- fa q_p), fb = S (values) or dS (deviations)
+            tacc += muh - (muf[0] * w0 * dS + dS * F1 + fa * Fdq);
+            aS = w0 * muf[0] + F1 + 3 * c.inv_cl * Fdq;
+            fbx = fa * Vf[0];
+            fby = fa * Vf[1];
+            fbz = fa * Vf[2];
         }
         tau_acc += (sizeof(T) == 4) ? (double)(tacc * (T)c.inv_tau2) : (double)tacc * c.inv_tau2;
-        T aS, fbx, fby, fbz;
-        f_eq_adjoint_S<T>(muf, Sfull, bx, by, bz, c.inv_cl, aS, fbx, fby, fbz);
         T vE, vx, vy, vz;
         recovery_adjoint<T>(ae, fbx + gbx, fby + gby, fbz + gbz, Et, sqt, Dt, bx, by, bz, mx, my, mz, vE, vx, vy, vz);
         // ---- nu = (1 - 1/tau) mu + (1/tau) P^T v, scattered (transpose of the pull) ----
@@ -625,7 +683,7 @@ static int adjoint_step_t(const Geom& g, const Phys& ph, const T* A, const T* Li
         return grid;
     };
     int grid = nb;
-    if (sizeof(T) == 8) {
+    if constexpr (sizeof(T) == 8) {
         switch (g.xbc) {
             case XBC_PERIODIC: grid = go(k_adjoint_step<T, XBC_PERIODIC, 2, false>, false, 2); break;
             case XBC_INFLOW_OUTFLOW: grid = go(k_adjoint_step<T, XBC_INFLOW_OUTFLOW, 2, false>, false, 2); break;
