@@ -45,6 +45,12 @@ def build(force: bool = False) -> str:
                "-std=c11", "-o", tmp, _SRC, "-lm"]
         subprocess.check_call(cmd)
         os.replace(tmp, so)
+        for f in os.listdir(_BUILD):
+            if f.startswith("librlb_oracle_") and f.endswith(".so") and os.path.join(_BUILD, f) != so:
+                try:
+                    os.remove(os.path.join(_BUILD, f))
+                except OSError:
+                    pass
     return so
 
 

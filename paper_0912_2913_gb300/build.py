@@ -86,6 +86,13 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     os.replace(tmp, so)
     for o, _ in results:
         os.remove(o)
+    # drop libraries of superseded sources
+    for f in os.listdir(BUILD):
+        if f.startswith("librlb_") and f.endswith(".so") and os.path.join(BUILD, f) != so:
+            try:
+                os.remove(os.path.join(BUILD, f))
+            except OSError:
+                pass
     return so
 
 
