@@ -170,6 +170,26 @@ RLB_API rlb_status rlb_adjoint_macro(rlb_ctx* ctx, const void* state, const doub
 RLB_API rlb_status rlb_adjoint_step(rlb_ctx* ctx, const void* state_t, const void* lam_in, void* lam_out,
                             double* dL_dtau_accum, double* dL_dbeta_in_accum);
 
+/* rlb_adjoint_step without any device allocation.  The paper has no
+ * counterpart: this is an interface for callers that cannot allocate device
+ * memory at the point of the call -- code running under a caching allocator
+ * or memory pool that owns all device memory, or a real-time loop that must
+ * not synchronise (cudaMalloc/cudaFree can synchronise the device).
+ * Same arguments, results and errors as rlb_adjoint_step, from the same
+ * kernels launched as a persistent grid (SMs x 2 blocks for FP64, x 4 for
+ * FP32, capped at N/128 blocks); the results agree with rlb_adjoint_step's
+ * to rounding (the sums are grouped by another grid).  The
+ * per-warp partial sums live in one static device array of 32768 doubles
+ * (256 KiB) per device: a launch that would need more (16 doubles per
+ * block) returns RLB_ERR_ARG and enqueues nothing; every launch writes all
+ * the slots it reads, so nothing needs to start at zero.  The first call on
+ * each device sets up the array's address (with that device current; make
+ * the first call before any stream capture); the context's device must be
+ * current.  Calls that overlap in time on one device (different streams or
+ * contexts) share the array and race: serialise them.                     */
+RLB_API rlb_status rlb_adjoint_step_noalloc(rlb_ctx* ctx, const void* state_t, const void* lam_in, void* lam_out,
+                                            double* dL_dtau_accum, double* dL_dbeta_in_accum);
+
 /* Gradient with respect to the initial fields of rlb_init_fields, given
  * lam0 = dL/dA_0 (device): writes dL/dn0, dL/deps0 (N) and dL/dbeta0 (3N),
  * zero at solid cells and at the inflow plane, whose dependence on beta_in

@@ -25,7 +25,7 @@ EXPORTS = (
     "rlb_state_layout", "rlb_workspace_bytes", "rlb_create", "rlb_destroy", "rlb_init_fields", "rlb_step",
     "rlb_step_into", "rlb_state_ptr", "rlb_save_state", "rlb_load_state", "rlb_macro", "rlb_stats",
     "rlb_adjoint_macro", "rlb_adjoint_step", "rlb_adjoint_fields", "rlb_sync", "rlb_status_str", "rlb_last_error",
-    "rlb_launch_count", "rlb_selftest_conversions",
+    "rlb_launch_count", "rlb_selftest_conversions", "rlb_adjoint_step_noalloc",
 )
 
 
@@ -85,6 +85,7 @@ def load(build_if_missing: bool = True):
             "rlb_stats": ([vp, P(i64), P(i64), P(i64), P(i64)], st),
             "rlb_adjoint_macro": ([vp, vp, dp, dp, dp, vp], st),
             "rlb_adjoint_step": ([vp, vp, vp, vp, dp, dp], st),
+            "rlb_adjoint_step_noalloc": ([vp, vp, vp, vp, dp, dp], st),
             "rlb_adjoint_fields": ([vp, dp, dp, dp, vp, dp, dp, dp, dp], st),
             "rlb_sync": ([vp], st),
             "rlb_status_str": ([ctypes.c_int], ctypes.c_char_p),
@@ -203,6 +204,11 @@ def rlb_adjoint_macro(ctx, state, dL_dn, dL_deps, dL_dbeta, lam_out) -> None:
 def rlb_adjoint_step(ctx, state_t, lam_in, lam_out, dL_dtau_accum, dL_dbeta_in_accum) -> None:
     _check(load().rlb_adjoint_step(ctx, _ptr(state_t), _ptr(lam_in), _ptr(lam_out), _ptr(dL_dtau_accum),
                                    _ptr(dL_dbeta_in_accum)), ctx)
+
+
+def rlb_adjoint_step_noalloc(ctx, state_t, lam_in, lam_out, dL_dtau_accum, dL_dbeta_in_accum) -> None:
+    _check(load().rlb_adjoint_step_noalloc(ctx, _ptr(state_t), _ptr(lam_in), _ptr(lam_out), _ptr(dL_dtau_accum),
+                                           _ptr(dL_dbeta_in_accum)), ctx)
 
 
 def rlb_adjoint_fields(ctx, n0, eps0, beta0, lam0, dL_dn0, dL_deps0, dL_dbeta0, dL_dbeta_in_accum) -> None:

@@ -24,6 +24,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "rlb_device.cuh"
 
 namespace rlb {
@@ -733,6 +735,102 @@ cudaError_t launch_adjoint_fields(int prec, const Geom& g, const Phys& ph, const
         k_adjoint_fields<float><<<nb, 128, 0, st>>>(n0, eps0, beta0, (const float*)A0, (const float*)lam0, dn0, deps0,
                                                     dbeta0, g, ph, red);
     k_finalize<<<1, 1024, 0, st>>>(red, nb, nullptr, dbeta_in);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free adjoint step.  Same kernels as launch_adjoint_step, always
+// as the persistent grid-stride launch (grid = SMs x resident blocks, capped
+// at the block count), with the per-warp partial sums in a fixed static
+// device array instead of the context workspace.  Every launch writes all
+// grid*16 slots it reads, so the array needs no zeroing; two launches that
+// overlap in time on one device (other streams, other contexts) share it and
+// race.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) double g_adj_scratch[kAdjScratchDoubles];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+double* g_scratch_ptr[kMaxDevices];
+int g_scratch_nsm[kMaxDevices];
+
+// Set-up once per device, with that device current: the device address of
+// g_adj_scratch and the SM count.
+cudaError_t scratch_for_device(int dev, double** ptr, int* nsm) {
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+        double* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress((void**)&p, g_adj_scratch);
+        if (e != cudaSuccess) return e;
+        int n = 0;
+        e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        g_scratch_nsm[dev] = n;
+        g_scratch_ptr[dev] = p;
+    }
+    *ptr = g_scratch_ptr[dev];
+    *nsm = g_scratch_nsm[dev];
+    return cudaSuccess;
+}
+
+template <typename T, int MINB>
+int adjoint_step_noalloc_t(const Geom& g, const Phys& ph, const T* A, const T* Li, T* Lo, double* red, int grid,
+                           const double* inflow_d, cudaStream_t st) {
+    AdjConst<T> c;
+    c.om = (T)ph.omega;
+    c.omw = (T)(1.0 - ph.omega);
+    c.c_l = (T)ph.c_l;
+    c.inv_cl = (T)ph.inv_cl;
+    c.inv_cl2 = (T)ph.inv_cl2;
+    c.n_ref = (T)ph.n_ref;
+    c.g0a = (T)(3.0 - 2.0 * ph.inv_cl2);
+    c.g0b = (T)(4.0 - 2.0 * ph.inv_cl2);
+    c.eps_ref = ph.eps_ref;
+    c.inv_tau2 = ph.omega * ph.omega;
+    switch (g.xbc) {
+        case XBC_PERIODIC:
+            k_adjoint_step<T, XBC_PERIODIC, MINB, true><<<grid, 128, 0, st>>>(A, Li, Lo, g, ph, c, red, inflow_d);
+            break;
+        case XBC_INFLOW_OUTFLOW:
+            k_adjoint_step<T, XBC_INFLOW_OUTFLOW, MINB, true><<<grid, 128, 0, st>>>(A, Li, Lo, g, ph, c, red,
+                                                                                   inflow_d);
+            break;
+        default:
+            k_adjoint_step<T, XBC_OUTFLOW_BOTH, MINB, true><<<grid, 128, 0, st>>>(A, Li, Lo, g, ph, c, red,
+                                                                                 inflow_d);
+            break;
+    }
+    return grid;
+}
+}  // namespace
+
+cudaError_t launch_adjoint_step_noalloc(int prec, const Geom& g, const Phys& ph, const void* A, const void* lam_in,
+                                        void* lam_out, const double* inflow_d, double* dtau, double* dbeta_in,
+                                        cudaStream_t st, long long* need_doubles) {
+    set_last_launch_count(0);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    double* red = nullptr;
+    int nsm = 0;
+    e = scratch_for_device(dev, &red, &nsm);
+    if (e != cudaSuccess) return e;
+    const int minb = prec == 0 ? 2 : 4;
+    const int nb = adj_blocks(g.N);
+    const int grid = nsm * minb < nb ? nsm * minb : nb;
+    const long long need = 16ll * grid;  // 4 warps x 4 partial sums per block
+    if (need_doubles) *need_doubles = need;
+    if (need > kAdjScratchDoubles) return cudaErrorInvalidValue;
+    set_last_launch_count(2);
+    if (prec == 0)
+        adjoint_step_noalloc_t<double, 2>(g, ph, (const double*)A, (const double*)lam_in, (double*)lam_out, red, grid,
+                                          inflow_d, st);
+    else
+        adjoint_step_noalloc_t<float, 4>(g, ph, (const float*)A, (const float*)lam_in, (float*)lam_out, red, grid,
+                                         inflow_d, st);
+    k_finalize<<<1, 1024, 0, st>>>(red, grid * 4, dtau, dbeta_in);
     return cudaGetLastError();
 }
 

@@ -488,6 +488,27 @@ rlb_status rlb_adjoint_step(rlb_ctx* c, const void* state_t, const void* lam_in,
                         "adjoint_step");
 }
 
+rlb_status rlb_adjoint_step_noalloc(rlb_ctx* c, const void* state_t, const void* lam_in, void* lam_out,
+                                    double* dL_dtau_accum, double* dL_dbeta_in_accum) {
+    RLB_LATCHED(c);
+    if (!state_t || !lam_in || !lam_out || lam_in == lam_out) return fail(c, RLB_ERR_ARG, "bad buffers");
+    if (!dL_dtau_accum || !dL_dbeta_in_accum) return fail(c, RLB_ERR_ARG, "accumulators are required");
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaGetDevice");
+    if (dev != c->device)
+        return fail(c, RLB_ERR_STATE, "rlb_adjoint_step_noalloc: the context's device %d is not current (%d is)",
+                    c->device, dev);
+    long long need = 0;
+    e = launch_adjoint_step_noalloc(c->p.prec, c->g, c->ph, state_t, lam_in, lam_out, c->inflow_d, dL_dtau_accum,
+                                    dL_dbeta_in_accum, c->stream, &need);
+    if (e == cudaErrorInvalidValue && need > kAdjScratchDoubles)
+        return fail(c, RLB_ERR_ARG,
+                    "rlb_adjoint_step_noalloc: the launch needs %lld scratch doubles, the static maximum is %lld",
+                    need, kAdjScratchDoubles);
+    return after_launch(c, e, "adjoint_step_noalloc");
+}
+
 rlb_status rlb_adjoint_fields(rlb_ctx* c, const double* n0, const double* eps0, const double* beta0, const void* lam0,
                               double* dL_dn0, double* dL_deps0, double* dL_dbeta0, double* dL_dbeta_in_accum) {
     RLB_LATCHED(c);

@@ -90,6 +90,15 @@ cudaError_t launch_adjoint_macro(int prec, const Geom& g, const Phys& ph, const 
 cudaError_t launch_adjoint_step(int prec, const Geom& g, const Phys& ph, const void* A, const void* lam_in,
                                 void* lam_out, double* red, const double* inflow_d, double* dtau, double* dbeta_in,
                                 cudaStream_t stream);
+// Allocation-free variant of launch_adjoint_step (same kernels, persistent
+// grid): partial sums in a static device array of kAdjScratchDoubles doubles,
+// set up once per device on first use.  Needs 16 doubles per block of the
+// grid (reported in *need_doubles); returns cudaErrorInvalidValue, launching
+// nothing, when that exceeds the array.
+constexpr long long kAdjScratchDoubles = 32768;  // 256 KiB
+cudaError_t launch_adjoint_step_noalloc(int prec, const Geom& g, const Phys& ph, const void* A, const void* lam_in,
+                                        void* lam_out, const double* inflow_d, double* dtau, double* dbeta_in,
+                                        cudaStream_t stream, long long* need_doubles);
 // d eq_in / d beta_in table (38 x 3 doubles) of the inflow state.
 cudaError_t launch_inflow_derivs(const Phys& ph, double* out, cudaStream_t stream);
 cudaError_t launch_adjoint_fields(int prec, const Geom& g, const Phys& ph, const double* n0, const double* eps0,
