@@ -222,76 +222,279 @@ __device__ __noinline__ void eq_fields_adjoint(const double* muf, const double* 
 
 // ---------------------------------------------------------------------------
 // Step adjoint.  T = double: FP64 states and arithmetic.  T = float: FP32
-// deviation states; the recovery root runs in FP64 as in the forward FP32
-// kernel, everything else (equilibria, their adjoints, the recovery adjoint)
-// in binary32.  Two phases per cell (g, then f) keep the register footprint
-// near 60 values.
+// deviation states, binary32 arithmetic throughout (the recovery in the
+// cancellation-free deviation form of cell_g).  Per cell two phases, g then
+// f.  The per-cell mathematics (cell_g, cell_f, scatter_cell) is shared by
+// the register kernel and the shared-memory staged kernel.
 // ---------------------------------------------------------------------------
 template <typename T>
 struct AdjConst {
-    T om, omw, c_l, inv_cl, inv_cl2, n_ref, g0a, g0b;
-    double eps_ref, inv_tau2;
+    T om, omw, c_l, inv_cl, inv_cl2, n_ref, g0a, g0b, eps_ref_t, inv_tau2_t;
+    double inv_tau2;
 };
 
-// PIPE: persistent grid-stride loop that prefetches the next cell's state
-// gather and adjoint inputs into L2 while the current cell is processed;
+template <typename T>
+static AdjConst<T> make_adj_const(const Phys& ph) {
+    AdjConst<T> c;
+    c.om = (T)ph.omega;
+    c.omw = (T)(1.0 - ph.omega);
+    c.c_l = (T)ph.c_l;
+    c.inv_cl = (T)ph.inv_cl;
+    c.inv_cl2 = (T)ph.inv_cl2;
+    c.n_ref = (T)ph.n_ref;
+    c.g0a = (T)(3.0 - 2.0 * ph.inv_cl2);
+    c.g0b = (T)(4.0 - 2.0 * ph.inv_cl2);
+    c.eps_ref_t = (T)ph.eps_ref;
+    c.inv_tau2 = ph.omega * ph.omega;
+    c.inv_tau2_t = (T)c.inv_tau2;
+    return c;
+}
+
+// What the g phase leaves for the f phase and the recovery adjoint.
+template <typename T>
+struct CellG {
+    T mx, my, mz, Et, sqt, Dt, bx, by, bz;  // moments, recovery
+    T tacc, ae, gbx, gby, gbz;              // sum mu_g (h - eq), d/d eps, d/d beta
+};
+
+// Moments and recovery from the 19 g populations h, then the g part of the
+// collision adjoint at mu = mug.
+template <typename T>
+__device__ __forceinline__ void cell_g(const T* h, const T* mug, const AdjConst<T>& c, CellG<T>& r) {
+    T dE = h[0], dd[9];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        dE += h[2 * p + 1] + h[2 * p + 2];
+        dd[p] = h[2 * p + 1] - h[2 * p + 2];
+    }
+    const T mx = c.c_l * (dd[0] + dd[3] + dd[4] + dd[5] + dd[6]);
+    const T my = c.c_l * (dd[1] + dd[3] - dd[4] + dd[7] + dd[8]);
+    const T mz = c.c_l * (dd[2] + dd[5] - dd[6] + dd[7] - dd[8]);
+    T Et, sqt, Dt, epst, e0, bx, by, bz, b2, gam2;
+    if constexpr (sizeof(T) == 8) {
+        const double E = dE;
+        const double sq = sqrt(4.0 * E * E - 3.0 * (mx * mx + my * my + mz * mz));
+        const double eps = sq - E;
+        const double D = 3.0 * E + eps;
+        const double r3 = 3.0 / D;
+        bx = mx * r3;
+        by = my * r3;
+        bz = mz * r3;
+        b2 = bx * bx + by * by + bz * bz;
+        gam2 = 1.0 / (1.0 - b2);
+        Et = E;
+        sqt = sq;
+        Dt = D;
+        epst = eps;
+        e0 = eps;
+    } else {
+        // binary32 in deviation form (the coefficients of the adjoint need
+        // no FP64): E = eps_ref + dE, s = sqrt(E^2 - 3/4 M^2), eps = 2 s - E,
+        // and the deviation eps - eps_ref = 2 (s - eps_ref) - dE with
+        // s - eps_ref = (dE (2 eps_ref + dE) - 3/4 M^2) / (s + eps_ref),
+        // free of the cancellation of eps - eps_ref.
+        const float er = c.eps_ref_t;
+        const float m34 = 0.75f * fmaf(mx, mx, fmaf(my, my, mz * mz));
+        const float num = fmaf(dE, fmaf(2.0f, er, dE), -m34);
+        const float sr = sqrtf(fmaf(er, er, num));
+        e0 = fmaf(2.0f, __fdividef(num, sr + er), -dE);
+        epst = er + e0;
+        Et = er + dE;
+        sqt = 2.0f * sr;
+        Dt = fmaf(3.0f, Et, epst);
+        const float r3 = __fdividef(3.0f, Dt);
+        bx = mx * r3;
+        by = my * r3;
+        bz = mz * r3;
+        b2 = fmaf(bx, bx, fmaf(by, by, bz * bz));
+        gam2 = __fdividef(1.0f, 1.0f - b2);
+    }
+    const T q[9] = {bx, by, bz, bx + by, bx - by, bx + bz, bx - bz, by + bz, by - bz};
+    const T eg = epst * gam2;
+    // Everything the collision adjoint needs from mu reduces to a few
+    // weighted pair sums (sigma_p = mu_{+p} + mu_{-p}, delta_p = mu_{+p} -
+    // mu_{-p}, weight w_p, q_p = e_p . beta):
+    //   S1 = sum w sigma,  Sq2 = sum w sigma q^2,  Sdq = sum w delta q,
+    //   Vq = sum w sigma q e_p,  Vd = sum w delta e_p.
+    // With them (Eqs. equil2as/equil2bs and their derivatives):
+    //   sum mu_i geq_i = mu_0 geq_0 + k1 S1 + k2 Sq2 + k3 Sdq,
+    //   d/d eps = S1/c_l^2 + gamma^2 (SYM + ASY) + rest-particle term,
+    //   d/d gamma^2 = eps (SYM + ASY + rest term), d/d b2 = -2 eps gamma^2 (S1 + w0 mu_0)/c_l^2,
+    //   d/d beta = eps gamma^2 (12 Vq / c_l^2 + 4 Vd / c_l) + (chain through gamma^2 and b2) beta,
+    // SYM = (6 Sq2 - 2 b2 S1)/c_l^2, ASY = 4 Sdq / c_l; and likewise for f.
+    T muh = mug[0] * h[0];
+#pragma unroll
+    for (int i = 1; i < 19; ++i) muh += mug[i] * h[i];
+    T S1 = 0, Sq2 = 0, Sdq = 0, Vq[3] = {0, 0, 0}, Vd[3] = {0, 0, 0};
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        const T w = (T)pair_w(p);
+        const T ws = w * (mug[2 * p + 1] + mug[2 * p + 2]);
+        const T wd = w * (mug[2 * p + 1] - mug[2 * p + 2]);
+        S1 += ws;
+        const T wsq = ws * q[p];
+        Sq2 += wsq * q[p];
+        Sdq += wd * q[p];
+        const int ex = pair_ex(p), ey = pair_ey(p), ez = pair_ez(p);
+        if (ex) { Vq[0] += wsq; Vd[0] += wd; }
+        if (ey > 0) { Vq[1] += wsq; Vd[1] += wd; }
+        if (ey < 0) { Vq[1] -= wsq; Vd[1] -= wd; }
+        if (ez > 0) { Vq[2] += wsq; Vd[2] += wd; }
+        if (ez < 0) { Vq[2] -= wsq; Vd[2] -= wd; }
+    }
+    const T m0 = mug[0], w0 = (T)kW0;
+    const T k1 = (e0 - 2 * eg * b2) * c.inv_cl2, k2 = 6 * eg * c.inv_cl2, k3 = 4 * eg * c.inv_cl;
+    const T geq0 = (sizeof(T) == 8) ? w0 * (4 * eg - epst * (2 * c.inv_cl2 + 1) - 2 * eg * b2 * c.inv_cl2)
+                                    : w0 * (e0 * c.g0a + eg * b2 * c.g0b);
+    r.tacc = muh - (m0 * geq0 + k1 * S1 + k2 * Sq2 + k3 * Sdq);
+    const T SYM = (6 * Sq2 - 2 * b2 * S1) * c.inv_cl2;
+    const T ASY = 4 * c.inv_cl * Sdq;
+    r.ae = c.inv_cl2 * S1 + gam2 * (SYM + ASY) + w0 * m0 * (4 * gam2 - (2 * c.inv_cl2 + 1) - 2 * gam2 * b2 * c.inv_cl2);
+    const T gg2 = SYM + ASY + w0 * m0 * (4 - 2 * b2 * c.inv_cl2);
+    const T gb2 = -2 * gam2 * c.inv_cl2 * (S1 + w0 * m0);
+    const T rad = 2 * epst * (gb2 + gam2 * gam2 * gg2);
+    const T cq = eg * 12 * c.inv_cl2, cd = eg * 4 * c.inv_cl;
+    r.gbx = cq * Vq[0] + cd * Vd[0] + rad * bx;
+    r.gby = cq * Vq[1] + cd * Vd[1] + rad * by;
+    r.gbz = cq * Vq[2] + cd * Vd[2] + rad * bz;
+    r.mx = mx;
+    r.my = my;
+    r.mz = mz;
+    r.Et = Et;
+    r.sqt = sqt;
+    r.Dt = Dt;
+    r.bx = bx;
+    r.by = by;
+    r.bz = bz;
+}
+
+// The f part: sum mu_f (h - eq) and the adjoints of S = n gamma and beta.
+template <typename T>
+__device__ __forceinline__ void cell_f(const T* h, const T* muf, const CellG<T>& r, const AdjConst<T>& c, T& tacc,
+                                       T& aS, T& fbx, T& fby, T& fbz) {
+    const T q[9] = {r.bx, r.by, r.bz, r.bx + r.by, r.bx - r.by, r.bx + r.bz, r.bx - r.bz, r.by + r.bz, r.by - r.bz};
+    T dS = h[0];
+#pragma unroll
+    for (int i = 1; i < 19; ++i) dS += h[i];
+    const T Sfull = (sizeof(T) == 8) ? dS : dS + c.n_ref;
+    T muh = muf[0] * h[0];
+#pragma unroll
+    for (int i = 1; i < 19; ++i) muh += muf[i] * h[i];
+    T F1 = 0, Fdq = 0, Vf[3] = {0, 0, 0};
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        const T w = (T)pair_w(p);
+        const T ws = w * (muf[2 * p + 1] + muf[2 * p + 2]);
+        const T wd = w * (muf[2 * p + 1] - muf[2 * p + 2]);
+        F1 += ws;
+        Fdq += wd * q[p];
+        const int ex = pair_ex(p), ey = pair_ey(p), ez = pair_ez(p);
+        if (ex) Vf[0] += wd;
+        if (ey > 0) Vf[1] += wd;
+        if (ey < 0) Vf[1] -= wd;
+        if (ez > 0) Vf[2] += wd;
+        if (ez < 0) Vf[2] -= wd;
+    }
+    const T w0 = (T)kW0;
+    const T fa = 3 * Sfull * c.inv_cl;
+    // f^eq_{+-p} = w_p (fb +- fa q_p), fb = S (values) or dS (deviations)
+    tacc = muh - (muf[0] * w0 * dS + dS * F1 + fa * Fdq);
+    aS = w0 * muf[0] + F1 + 3 * c.inv_cl * Fdq;
+    fbx = fa * Vf[0];
+    fby = fa * Vf[1];
+    fbz = fa * Vf[2];
+}
+
+// nu = (1 - 1/tau) mu + (1/tau) P^T v for the 38 populations of the cell,
+// handed to put(plane, velocity, value) (the transpose of the pull).
+template <typename T, typename PUT>
+__device__ __forceinline__ void scatter_cell(const T* muf, const T* mug, T aS, T vE, T vx, T vy, T vz,
+                                             const AdjConst<T>& c, PUT put) {
+    const T nuS = c.om * aS, nuE = c.om * vE;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) put(i, i, c.omw * muf[i] + nuS);
+    put(19, 0, c.omw * mug[0] + nuE);
+    const T pm[9] = {vx, vy, vz, vx + vy, vx - vy, vx + vz, vx - vz, vy + vz, vy - vz};
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        const T t = c.om * c.c_l * pm[p];
+        put(20 + 2 * p, 2 * p + 1, c.omw * mug[2 * p + 1] + nuE + t);
+        put(21 + 2 * p, 2 * p + 2, c.omw * mug[2 * p + 2] + nuE - t);
+    }
+}
+
+// A ghost plane cell (non-periodic x): nobody reads its populations that do
+// not point into the lattice; the others are written by the scatter of x +- 1.
+// At the inflow plane (held at eq(n_in, eps_in, beta_in)) its adjoint adds
+// lambda_{t+1} . d eq_in / d beta_in (a per-context table).
+template <typename T, int XBC>
+__device__ __forceinline__ void ghost_cell(int x, int idx, long long S, const T* __restrict__ A,
+                                           const T* __restrict__ Lin, T* __restrict__ Lout,
+                                           const double* __restrict__ inflow_d, double& bin0, double& bin1,
+                                           double& bin2, bool& has_b) {
+    const int inward = (x == 0) ? 1 : -1;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        if (vel_x(i) != inward) {
+            Lout[i * S + idx] = (T)0;
+            Lout[(19 + i) * S + idx] = (T)0;
+        }
+    }
+    if (XBC == XBC_INFLOW_OUTFLOW && x == 0 && !is_solid(A[idx])) {
+        T a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll 2
+        for (int q = 0; q < 38; ++q) {
+            const T l = Lin[q * S + idx];
+            a0 += l * (T)inflow_d[3 * q + 0];
+            a1 += l * (T)inflow_d[3 * q + 1];
+            a2 += l * (T)inflow_d[3 * q + 2];
+        }
+        bin0 += (double)a0;
+        bin1 += (double)a1;
+        bin2 += (double)a2;
+        has_b = true;
+    }
+}
+
+// Populations of x that a ghost plane would pull: nobody reads them.
+template <typename T, int XBC>
+__device__ __forceinline__ void zero_to_ghost(int x, int nx, int idx, long long S, T* __restrict__ Lout) {
+    if (XBC != XBC_PERIODIC && (x == 1 || x == nx - 2)) {
+#pragma unroll
+        for (int i = 1; i < 19; ++i) {
+            const bool to_ghost = (x == 1 && vel_x(i) == -1) || (x == nx - 2 && vel_x(i) == 1);
+            if (to_ghost) {
+                Lout[i * S + idx] = (T)0;
+                Lout[(19 + i) * S + idx] = (T)0;
+            }
+        }
+    }
+}
+
+// mu offset of the outflow ghost that copies x (0 if none)
+template <int XBC>
+__device__ __forceinline__ int dup_of(int x, int nx) {
+    return (XBC != XBC_PERIODIC && x == nx - 2) ? 1 : ((XBC == XBC_OUTFLOW_BOTH && x == 1) ? -1 : 0);
+}
+
+// Register kernel.  PIPE: persistent grid-stride loop over the cells;
 // otherwise one cell per thread.
 template <typename T, int XBC, int MINB, bool PIPE>
 __global__ void __launch_bounds__(128, MINB)
     k_adjoint_step(const T* __restrict__ A, const T* __restrict__ Lin, T* __restrict__ Lout, Geom g, Phys ph,
                    AdjConst<T> c, double* red, const double* __restrict__ inflow_d) {
     const long long S = g.S;
-    double tau_acc = 0.0, bin0 = 0.0, bin1 = 0.0, bin2 = 0.0;
+    T tau_acc = 0;
+    double bin0 = 0.0, bin1 = 0.0, bin2 = 0.0;
     bool has_b = false;
     const int stride = PIPE ? gridDim.x * blockDim.x : g.N;
-    auto prefetch_cell = [&](int cidx) {
-        int x, y, z;
-        cell_coords(g, cidx, x, y, z);
-        if (XBC != XBC_PERIODIC && (x == 0 || x == g.nx - 1)) return;
-        const PullOffsets o(g, x, y, z);
-#pragma unroll
-        for (int i = 0; i < 19; ++i) {
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(A + (19 + i) * S + cidx + o.src(i)));
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(A + i * S + cidx + o.src(i)));
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(Lin + (19 + i) * S + cidx));
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(Lin + i * S + cidx));
-        }
-    };
-    if (PIPE && blockIdx.x * blockDim.x + threadIdx.x < g.N) prefetch_cell(blockIdx.x * blockDim.x + threadIdx.x);
     // the loop ends for every thread before the warp reduction ('continue'
     // skips to the next cell)
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < g.N; idx += stride) {
-        if (PIPE && idx + stride < g.N) prefetch_cell(idx + stride);
         int x, y, z;
         cell_coords(g, idx, x, y, z);
-        const bool ghost = (XBC != XBC_PERIODIC) && (x == 0 || x == g.nx - 1);
-        if (ghost) {
-            // Nobody reads the ghost's populations that do not point into the
-            // lattice; the others are written by the scatter of x +- 1.
-            const int inward = (x == 0) ? 1 : -1;
-#pragma unroll
-            for (int i = 0; i < 19; ++i) {
-                if (vel_x(i) != inward) {
-                    Lout[i * S + idx] = (T)0;
-                    Lout[(19 + i) * S + idx] = (T)0;
-                }
-            }
-            if (XBC == XBC_INFLOW_OUTFLOW && x == 0 && !is_solid(A[idx])) {
-                // the inflow plane holds eq(n_in, eps_in, beta_in): its adjoint
-                // adds lambda_{t+1} . d eq_in / d beta_in (a per-context table)
-                T a0 = 0, a1 = 0, a2 = 0;
-#pragma unroll 2
-                for (int q = 0; q < 38; ++q) {
-                    const T l = Lin[q * S + idx];
-                    a0 += l * (T)inflow_d[3 * q + 0];
-                    a1 += l * (T)inflow_d[3 * q + 1];
-                    a2 += l * (T)inflow_d[3 * q + 2];
-                }
-                bin0 += (double)a0;
-                bin1 += (double)a1;
-                bin2 += (double)a2;
-                has_b = true;
-            }
+        if ((XBC != XBC_PERIODIC) && (x == 0 || x == g.nx - 1)) {
+            ghost_cell<T, XBC>(x, idx, S, A, Lin, Lout, inflow_d, bin0, bin1, bin2, has_b);
             continue;
         }
         if (is_solid(A[19 * S + idx])) {  // never updated: identity
@@ -301,7 +504,7 @@ __global__ void __launch_bounds__(128, MINB)
         }
         const PullOffsets o(g, x, y, z);
         // mu = lambda_{t+1}(x), plus the outflow ghost that copies x
-        const int dup = (XBC != XBC_PERIODIC && x == g.nx - 2) ? 1 : ((XBC == XBC_OUTFLOW_BOTH && x == 1) ? -1 : 0);
+        const int dup = dup_of<XBC>(x, g.nx);
         // rare cases (a cell copied by an outflow ghost, links to solid cells)
         // take branches, so the common cell runs straight-line loads/stores
         auto load_mu = [&](T* mu, int base) {
@@ -320,7 +523,7 @@ __global__ void __launch_bounds__(128, MINB)
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(Lin + i * S + idx));
             }
         }
-        // ---- phase 1: g -- gather, moments, recovery, g part of dL/dtau and of the adjoint
+        // ---- g phase: gather, moments, recovery, g part of the adjoint
         unsigned bounced = 0u;
         T h[19];
 #pragma unroll
@@ -341,108 +544,11 @@ __global__ void __launch_bounds__(128, MINB)
                 }
             }
         }
-        T dE = h[0], dd[9];
-#pragma unroll
-        for (int p = 0; p < 9; ++p) {
-            dE += h[2 * p + 1] + h[2 * p + 2];
-            dd[p] = h[2 * p + 1] - h[2 * p + 2];
-        }
-        const T mx = c.c_l * (dd[0] + dd[3] + dd[4] + dd[5] + dd[6]);
-        const T my = c.c_l * (dd[1] + dd[3] - dd[4] + dd[7] + dd[8]);
-        const T mz = c.c_l * (dd[2] + dd[5] - dd[6] + dd[7] - dd[8]);
-        T Et, sqt, Dt, epst, e0, bx, by, bz, b2, gam2;
-        if constexpr (sizeof(T) == 8) {
-            const double E = dE;
-            const double sq = sqrt(4.0 * E * E - 3.0 * (mx * mx + my * my + mz * mz));
-            const double eps = sq - E;
-            const double D = 3.0 * E + eps;
-            const double r3 = 3.0 / D;
-            bx = mx * r3;
-            by = my * r3;
-            bz = mz * r3;
-            b2 = bx * bx + by * by + bz * bz;
-            gam2 = 1.0 / (1.0 - b2);
-            Et = E;
-            sqt = sq;
-            Dt = D;
-            epst = eps;
-            e0 = eps;
-        } else {
-            // as in the forward FP32 collision: FP64 root, conversions on the ALU
-            const double E = c.eps_ref + f2d(dE);
-            const double Mx = f2d(mx), My = f2d(my), Mz = f2d(mz);
-            const double d4 = fma(E, E, -0.75 * fma(Mx, Mx, fma(My, My, Mz * Mz)));
-            const float y0 = rsqrtf(d2f_seed(d4));
-            const double s0 = d4 * f2d(y0);
-            const double s = fma(fma(-s0, s0, d4), f2d(0.5f * y0), s0);
-            const double eps = fma(2.0, s, -E);
-            Dt = d2f(fma(3.0, E, eps));
-            e0 = d2f(eps - c.eps_ref);
-            epst = d2f(eps);
-            Et = d2f(E);
-            sqt = d2f(2.0 * s);
-            const float r3 = 3.0f / Dt;
-            bx = mx * r3;
-            by = my * r3;
-            bz = mz * r3;
-            b2 = fmaf(bx, bx, fmaf(by, by, bz * bz));
-            gam2 = 1.0f / (1.0f - b2);
-        }
-        const T q[9] = {bx, by, bz, bx + by, bx - by, bx + bz, bx - bz, by + bz, by - bz};
-        const T eg = epst * gam2;
-        // Everything the collision adjoint needs from mu reduces to a few
-        // weighted pair sums (sigma_p = mu_{+p} + mu_{-p}, delta_p = mu_{+p} -
-        // mu_{-p}, weight w_p, q_p = e_p . beta):
-        //   S1 = sum w sigma,  Sq2 = sum w sigma q^2,  Sdq = sum w delta q,
-        //   Vq = sum w sigma q e_p,  Vd = sum w delta e_p.
-        // With them (Eqs. equil2as/equil2bs and their derivatives):
-        //   sum mu_i geq_i = mu_0 geq_0 + k1 S1 + k2 Sq2 + k3 Sdq,
-        //   d/d eps = S1/c_l^2 + gamma^2 (SYM + ASY) + rest-particle term,
-        //   d/d gamma^2 = eps (SYM + ASY + rest term), d/d b2 = -2 eps gamma^2 (S1 + w0 mu_0)/c_l^2,
-        //   d/d beta = eps gamma^2 (12 Vq / c_l^2 + 4 Vd / c_l) + (chain through gamma^2 and b2) beta,
-        // SYM = (6 Sq2 - 2 b2 S1)/c_l^2, ASY = 4 Sdq / c_l; and likewise for f.
         T mug[19];
         load_mu(mug, 19);
-        T tacc;  // sum mu (h - eq), both sets
-        T ae, gbx, gby, gbz;
-        {
-            T muh = mug[0] * h[0];
-#pragma unroll
-            for (int i = 1; i < 19; ++i) muh += mug[i] * h[i];
-            T S1 = 0, Sq2 = 0, Sdq = 0, Vq[3] = {0, 0, 0}, Vd[3] = {0, 0, 0};
-#pragma unroll
-            for (int p = 0; p < 9; ++p) {
-                const T w = (T)pair_w(p);
-                const T ws = w * (mug[2 * p + 1] + mug[2 * p + 2]);
-                const T wd = w * (mug[2 * p + 1] - mug[2 * p + 2]);
-                S1 += ws;
-                const T wsq = ws * q[p];
-                Sq2 += wsq * q[p];
-                Sdq += wd * q[p];
-                const int ex = pair_ex(p), ey = pair_ey(p), ez = pair_ez(p);
-                if (ex) { Vq[0] += wsq; Vd[0] += wd; }
-                if (ey > 0) { Vq[1] += wsq; Vd[1] += wd; }
-                if (ey < 0) { Vq[1] -= wsq; Vd[1] -= wd; }
-                if (ez > 0) { Vq[2] += wsq; Vd[2] += wd; }
-                if (ez < 0) { Vq[2] -= wsq; Vd[2] -= wd; }
-            }
-            const T m0 = mug[0], w0 = (T)kW0;
-            const T k1 = (e0 - 2 * eg * b2) * c.inv_cl2, k2 = 6 * eg * c.inv_cl2, k3 = 4 * eg * c.inv_cl;
-            const T geq0 = (sizeof(T) == 8) ? w0 * (4 * eg - epst * (2 * c.inv_cl2 + 1) - 2 * eg * b2 * c.inv_cl2)
-                                            : w0 * (e0 * c.g0a + eg * b2 * c.g0b);
-            tacc = muh - (m0 * geq0 + k1 * S1 + k2 * Sq2 + k3 * Sdq);
-            const T SYM = (6 * Sq2 - 2 * b2 * S1) * c.inv_cl2;
-            const T ASY = 4 * c.inv_cl * Sdq;
-            ae = c.inv_cl2 * S1 + gam2 * (SYM + ASY) + w0 * m0 * (4 * gam2 - (2 * c.inv_cl2 + 1) - 2 * gam2 * b2 * c.inv_cl2);
-            const T gg2 = SYM + ASY + w0 * m0 * (4 - 2 * b2 * c.inv_cl2);
-            const T gb2 = -2 * gam2 * c.inv_cl2 * (S1 + w0 * m0);
-            const T rad = 2 * epst * (gb2 + gam2 * gam2 * gg2);
-            const T cq = eg * 12 * c.inv_cl2, cd = eg * 4 * c.inv_cl;
-            gbx = cq * Vq[0] + cd * Vd[0] + rad * bx;
-            gby = cq * Vq[1] + cd * Vd[1] + rad * by;
-            gbz = cq * Vq[2] + cd * Vd[2] + rad * bz;
-        }
-        // ---- phase 2: f -- gather, S, f part of dL/dtau and of the adjoint
+        CellG<T> r;
+        cell_g(h, mug, c, r);
+        // ---- f phase
 #pragma unroll
         for (int i = 0; i < 19; ++i) h[i] = A[i * S + idx + o.src(i)];
         if (bounced) {
@@ -450,78 +556,177 @@ __global__ void __launch_bounds__(128, MINB)
             for (int i = 1; i < 19; ++i)
                 if ((bounced >> i) & 1u) h[i] = A[opp(i) * S + idx];
         }
-        T dS = h[0];
-#pragma unroll
-        for (int i = 1; i < 19; ++i) dS += h[i];
-        const T Sfull = (sizeof(T) == 8) ? dS : dS + c.n_ref;
         T muf[19];
         load_mu(muf, 0);
-        T aS, fbx, fby, fbz;
-        {
-            T muh = muf[0] * h[0];
-#pragma unroll
-            for (int i = 1; i < 19; ++i) muh += muf[i] * h[i];
-            T F1 = 0, Fdq = 0, Vf[3] = {0, 0, 0};
-#pragma unroll
-            for (int p = 0; p < 9; ++p) {
-                const T w = (T)pair_w(p);
-                const T ws = w * (muf[2 * p + 1] + muf[2 * p + 2]);
-                const T wd = w * (muf[2 * p + 1] - muf[2 * p + 2]);
-                F1 += ws;
-                Fdq += wd * q[p];
-                const int ex = pair_ex(p), ey = pair_ey(p), ez = pair_ez(p);
-                if (ex) Vf[0] += wd;
-                if (ey > 0) Vf[1] += wd;
-                if (ey < 0) Vf[1] -= wd;
-                if (ez > 0) Vf[2] += wd;
-                if (ez < 0) Vf[2] -= wd;
-            }
-            const T w0 = (T)kW0;
-            const T fa = 3 * Sfull * c.inv_cl;
-            // f^eq_{+-p} = w_p (fb +- fa q_p), fb = S (values) or dS (deviations)
-            tacc += muh - (muf[0] * w0 * dS + dS * F1 + fa * Fdq);
-            aS = w0 * muf[0] + F1 + 3 * c.inv_cl * Fdq;
-            fbx = fa * Vf[0];
-            fby = fa * Vf[1];
-            fbz = fa * Vf[2];
-        }
-        tau_acc += (sizeof(T) == 4) ? (double)(tacc * (T)c.inv_tau2) : (double)tacc * c.inv_tau2;
+        T tf, aS, fbx, fby, fbz;
+        cell_f(h, muf, r, c, tf, aS, fbx, fby, fbz);
+        tau_acc += (r.tacc + tf) * c.inv_tau2_t;
         T vE, vx, vy, vz;
-        recovery_adjoint<T>(ae, fbx + gbx, fby + gby, fbz + gbz, Et, sqt, Dt, bx, by, bz, mx, my, mz, vE, vx, vy, vz);
-        // ---- nu = (1 - 1/tau) mu + (1/tau) P^T v, scattered (transpose of the pull) ----
-        const T nuS = c.om * aS, nuE = c.om * vE;
-        auto scatter = [&](int q, int i, T v) {
+        recovery_adjoint<T>(r.ae, fbx + r.gbx, fby + r.gby, fbz + r.gbz, r.Et, r.sqt, r.Dt, r.bx, r.by, r.bz, r.mx,
+                            r.my, r.mz, vE, vx, vy, vz);
+        scatter_cell(muf, mug, aS, vE, vx, vy, vz, c, [&](int q, int i, T v) {
             if ((bounced >> i) & 1u)
                 Lout[(q - i + opp(i)) * S + idx] = v;
             else
                 Lout[q * S + idx + o.src(i)] = v;
-        };
-        Lout[idx] = c.omw * muf[0] + nuS;
-#pragma unroll
-        for (int i = 1; i < 19; ++i) scatter(i, i, c.omw * muf[i] + nuS);
-        Lout[19 * S + idx] = c.omw * mug[0] + nuE;
-        {
-            const T pm[9] = {vx, vy, vz, vx + vy, vx - vy, vx + vz, vx - vz, vy + vz, vy - vz};
-#pragma unroll
-            for (int p = 0; p < 9; ++p) {
-                const T t = c.om * c.c_l * pm[p];
-                scatter(20 + 2 * p, 2 * p + 1, c.omw * mug[2 * p + 1] + nuE + t);
-                scatter(21 + 2 * p, 2 * p + 2, c.omw * mug[2 * p + 2] + nuE - t);
-            }
-        }
-        // populations of x that a ghost plane would pull: nobody reads them
-        if (XBC != XBC_PERIODIC && (x == 1 || x == g.nx - 2)) {
-#pragma unroll
-            for (int i = 1; i < 19; ++i) {
-                const bool to_ghost = (x == 1 && vel_x(i) == -1) || (x == g.nx - 2 && vel_x(i) == 1);
-                if (to_ghost) {
-                    Lout[i * S + idx] = (T)0;
-                    Lout[(19 + i) * S + idx] = (T)0;
-                }
-            }
-        }
+        });
+        zero_to_ghost<T, XBC>(x, g.nx, idx, S, Lout);
     }
-    warp_partials<T>(tau_acc, bin0, bin1, bin2, has_b, red);
+    warp_partials<T>((double)tau_acc, bin0, bin1, bin2, has_b, red);
+}
+
+// ---------------------------------------------------------------------------
+// Shared-memory staged FP32 kernel.  Persistent grid-stride loop; every
+// thread stages the 38 values of each phase of its cells (19 pulled
+// populations + 19 lambda_{t+1}) in its own column of a three-slot ring with
+// 4-byte cp.async copies, one phase ahead of the arithmetic:
+//
+//     issue F_k | wait G_k, compute G_k | issue G_k+1 | wait F_k, compute F_k, scatter
+//
+// so the loads of the next phase are in flight during the arithmetic of the
+// current one without holding registers.  Slots: G_k, F_k, G_k+1 (the G slot
+// stays valid through F_k, whose scatter reads mu_g).  Each thread reads only
+// the slots it wrote, so cp.async.wait_group alone orders the accesses.
+// ---------------------------------------------------------------------------
+constexpr int kStageThreads = 128;
+constexpr int kStageSlots = 3;
+constexpr size_t kStageSmemBytes = sizeof(float) * kStageSlots * 38 * kStageThreads;
+
+__device__ __forceinline__ void cp_async4(uint32_t saddr, const void* gptr) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(saddr), "l"(gptr) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <int XBC>
+__global__ void __launch_bounds__(kStageThreads, 3)
+    k_adjoint_step_staged(const float* __restrict__ A, const float* __restrict__ Lin, float* __restrict__ Lout,
+                          Geom g, Phys ph, AdjConst<float> c, double* red, const double* __restrict__ inflow_d) {
+    extern __shared__ float stage[];  // [slot][value 0..37][thread]
+    const long long S = g.S;
+    const int tid = threadIdx.x;
+    const int stride = gridDim.x * blockDim.x;
+    const uint32_t scol = (uint32_t)__cvta_generic_to_shared(stage) + 4u * tid;
+    auto sval = [&](int slot, int q) -> float { return stage[(slot * 38 + q) * kStageThreads + tid]; };
+    auto is_ghost = [&](int x) { return XBC != XBC_PERIODIC && (x == 0 || x == g.nx - 1); };
+    // one phase (base 19: g, base 0: f) of the cell at (x, y, z) into a slot
+    auto issue = [&](int cidx, int x, int y, int z, int base, int slot) {
+        const PullOffsets o(g, x, y, z);
+        const uint32_t s0 = scol + 4u * (uint32_t)(slot * 38 * kStageThreads);
+#pragma unroll
+        for (int i = 0; i < 19; ++i)
+            cp_async4(s0 + 4u * (uint32_t)(i * kStageThreads), A + (base + i) * S + cidx + o.src(i));
+#pragma unroll
+        for (int i = 0; i < 19; ++i)
+            cp_async4(s0 + 4u * (uint32_t)((19 + i) * kStageThreads), Lin + (base + i) * S + cidx);
+    };
+
+    float tau_acc = 0.0f;
+    double bin0 = 0.0, bin1 = 0.0, bin2 = 0.0;
+    bool has_b = false;
+    int idx = blockIdx.x * blockDim.x + tid;
+    int x = 0, y = 0, z = 0;
+    if (idx < g.N) {
+        cell_coords(g, idx, x, y, z);
+        if (!is_ghost(x)) issue(idx, x, y, z, 19, 0);
+    }
+    cp_async_commit();
+    int sg = 0;
+    for (; idx < g.N; idx += stride) {
+        const int sf = sg == kStageSlots - 1 ? 0 : sg + 1;
+        const int sn = sf == kStageSlots - 1 ? 0 : sf + 1;
+        const bool ghost = is_ghost(x);
+        if (!ghost) issue(idx, x, y, z, 0, sf);
+        cp_async_commit();
+        const int nidx = idx + stride;
+        int xn = 0, yn = 0, zn = 0;
+        if (nidx < g.N) cell_coords(g, nidx, xn, yn, zn);
+        cp_async_wait<1>();  // G_k has landed
+        // ---- g phase
+        unsigned bounced = 0u;
+        bool solid = false;
+        const int dup = dup_of<XBC>(x, g.nx);
+        float mug[19];
+        CellG<float> r;
+        if (!ghost) {
+            float h[19];
+#pragma unroll
+            for (int i = 0; i < 19; ++i) h[i] = sval(sg, i);
+            solid = is_solid(h[0]);  // the cell's own g_0 (pull offset 0)
+            if (!solid) {
+                float sum = h[0];
+#pragma unroll
+                for (int i = 1; i < 19; ++i) sum += h[i];
+                if (isnan(sum)) {
+#pragma unroll
+                    for (int i = 1; i < 19; ++i) {
+                        if (is_solid(h[i])) {
+                            bounced |= 1u << i;
+                            h[i] = A[(19 + opp(i)) * S + idx];
+                        }
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 19; ++i) mug[i] = sval(sg, 19 + i);
+                if (dup) {
+#pragma unroll
+                    for (int i = 0; i < 19; ++i) mug[i] += Lin[(19 + i) * S + idx + dup];
+                }
+                cell_g(h, mug, c, r);
+            }
+        }
+        if (nidx < g.N && !is_ghost(xn)) issue(nidx, xn, yn, zn, 19, sn);
+        cp_async_commit();
+        cp_async_wait<1>();  // F_k has landed
+        // ---- f phase, scatter
+        if (ghost) {
+            ghost_cell<float, XBC>(x, idx, S, A, Lin, Lout, inflow_d, bin0, bin1, bin2, has_b);
+        } else if (solid) {  // never updated: identity
+#pragma unroll
+            for (int i = 0; i < 19; ++i) {
+                Lout[i * S + idx] = sval(sf, 19 + i);
+                Lout[(19 + i) * S + idx] = sval(sg, 19 + i);
+            }
+        } else {
+            const PullOffsets o(g, x, y, z);
+            float h[19], muf[19];
+#pragma unroll
+            for (int i = 0; i < 19; ++i) h[i] = sval(sf, i);
+            if (bounced) {
+#pragma unroll
+                for (int i = 1; i < 19; ++i)
+                    if ((bounced >> i) & 1u) h[i] = A[opp(i) * S + idx];
+            }
+#pragma unroll
+            for (int i = 0; i < 19; ++i) muf[i] = sval(sf, 19 + i);
+            if (dup) {
+#pragma unroll
+                for (int i = 0; i < 19; ++i) muf[i] += Lin[i * S + idx + dup];
+            }
+            float tf, aS, fbx, fby, fbz;
+            cell_f(h, muf, r, c, tf, aS, fbx, fby, fbz);
+            tau_acc += (r.tacc + tf) * c.inv_tau2_t;
+            float vE, vx, vy, vz;
+            recovery_adjoint<float>(r.ae, fbx + r.gbx, fby + r.gby, fbz + r.gbz, r.Et, r.sqt, r.Dt, r.bx, r.by,
+                                    r.bz, r.mx, r.my, r.mz, vE, vx, vy, vz);
+            scatter_cell(muf, mug, aS, vE, vx, vy, vz, c, [&](int q, int i, float v) {
+                if ((bounced >> i) & 1u)
+                    Lout[(q - i + opp(i)) * S + idx] = v;
+                else
+                    Lout[q * S + idx + o.src(i)] = v;
+            });
+            zero_to_ghost<float, XBC>(x, g.nx, idx, S, Lout);
+        }
+        sg = sn;
+        x = xn;
+        y = yn;
+        z = zn;
+    }
+    cp_async_wait<0>();
+    warp_partials<float>((double)tau_acc, bin0, bin1, bin2, has_b, red);
 }
 
 // d eq_j(n_in, eps_in, beta_in) / d beta_in,a for the 38 populations (one
@@ -642,7 +847,6 @@ __global__ void __launch_bounds__(128) k_adjoint_fields(const double* __restrict
 // Launchers
 // ---------------------------------------------------------------------------
 static inline int adj_blocks(int N) { return (N + 127) / 128; }
-static inline int adj_warps(int N) { return 4 * adj_blocks(N); }
 
 cudaError_t launch_adjoint_macro(int prec, const Geom& g, const Phys& ph, const void* A, const double* dn,
                                  const double* deps, const double* dbeta, void* lam, cudaStream_t st) {
@@ -658,33 +862,45 @@ cudaError_t launch_adjoint_macro(int prec, const Geom& g, const Phys& ph, const 
 template <typename T>
 static int adjoint_step_t(const Geom& g, const Phys& ph, const T* A, const T* Li, T* Lo, double* red, int nb,
                           const double* inflow_d, cudaStream_t st) {
-    AdjConst<T> c;
-    c.om = (T)ph.omega;
-    c.omw = (T)(1.0 - ph.omega);
-    c.c_l = (T)ph.c_l;
-    c.inv_cl = (T)ph.inv_cl;
-    c.inv_cl2 = (T)ph.inv_cl2;
-    c.n_ref = (T)ph.n_ref;
-    c.g0a = (T)(3.0 - 2.0 * ph.inv_cl2);
-    c.g0b = (T)(4.0 - 2.0 * ph.inv_cl2);
-    c.eps_ref = ph.eps_ref;
-    c.inv_tau2 = ph.omega * ph.omega;
-    auto go = [&](auto kern, bool pipe, int minb) {
-        int grid = nb;
-        if (pipe) {
-            static int nsm = 0;
-            if (nsm == 0) {
-                int dev = 0;
-                cudaGetDevice(&dev);
-                cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-            }
-            const int pg = nsm * minb;
-            grid = pg < nb ? pg : nb;
+    const AdjConst<T> c = make_adj_const<T>(ph);
+    auto persistent_grid = [&](int minb) {
+        static int nsm = 0;
+        if (nsm == 0) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         }
+        const int pg = nsm * minb;
+        return pg < nb ? pg : nb;
+    };
+    auto go = [&](auto kern, bool pipe, int minb) {
+        const int grid = pipe ? persistent_grid(minb) : nb;
         kern<<<grid, 128, 0, st>>>(A, Li, Lo, g, ph, c, red, inflow_d);
         return grid;
     };
     int grid = nb;
+    if constexpr (sizeof(T) == 4) {
+        if (g.adj_pipe == 2) {
+            auto staged = [&](auto kern) {
+                // the shared-memory opt-in, once per device and kernel
+                static unsigned char attr[64][3];
+                int dev = 0;
+                cudaGetDevice(&dev);
+                if (dev >= 0 && dev < 64 && !attr[dev][g.xbc]) {
+                    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageSmemBytes);
+                    attr[dev][g.xbc] = 1;
+                }
+                const int grid = persistent_grid(3);
+                kern<<<grid, kStageThreads, kStageSmemBytes, st>>>(A, Li, Lo, g, ph, c, red, inflow_d);
+                return grid;
+            };
+            switch (g.xbc) {
+                case XBC_PERIODIC: return staged(k_adjoint_step_staged<XBC_PERIODIC>);
+                case XBC_INFLOW_OUTFLOW: return staged(k_adjoint_step_staged<XBC_INFLOW_OUTFLOW>);
+                default: return staged(k_adjoint_step_staged<XBC_OUTFLOW_BOTH>);
+            }
+        }
+    }
     if constexpr (sizeof(T) == 8) {
         switch (g.xbc) {
             case XBC_PERIODIC: grid = go(k_adjoint_step<T, XBC_PERIODIC, 2, false>, false, 2); break;
@@ -778,17 +994,7 @@ cudaError_t scratch_for_device(int dev, double** ptr, int* nsm) {
 template <typename T, int MINB>
 int adjoint_step_noalloc_t(const Geom& g, const Phys& ph, const T* A, const T* Li, T* Lo, double* red, int grid,
                            const double* inflow_d, cudaStream_t st) {
-    AdjConst<T> c;
-    c.om = (T)ph.omega;
-    c.omw = (T)(1.0 - ph.omega);
-    c.c_l = (T)ph.c_l;
-    c.inv_cl = (T)ph.inv_cl;
-    c.inv_cl2 = (T)ph.inv_cl2;
-    c.n_ref = (T)ph.n_ref;
-    c.g0a = (T)(3.0 - 2.0 * ph.inv_cl2);
-    c.g0b = (T)(4.0 - 2.0 * ph.inv_cl2);
-    c.eps_ref = ph.eps_ref;
-    c.inv_tau2 = ph.omega * ph.omega;
+    const AdjConst<T> c = make_adj_const<T>(ph);
     switch (g.xbc) {
         case XBC_PERIODIC:
             k_adjoint_step<T, XBC_PERIODIC, MINB, true><<<grid, 128, 0, st>>>(A, Li, Lo, g, ph, c, red, inflow_d);

@@ -38,8 +38,7 @@ struct Geom {
     int variant; // launch variant of the one-cell-per-thread FP32 step (tuning)
     int pipe_blocks;  // resident blocks per SM of the persistent variant (tuning)
     FastDiv div_nx, div_ny;
-    int adj_minb;  // resident 128-thread blocks per SM the FP32 adjoint is built for (tuning)
-    int adj_pipe;  // 1: persistent FP32 adjoint with next-cell L2 prefetch (tuning)
+    int adj_pipe;  // FP32 adjoint kernel: 0 one cell per thread, 1 persistent, 2 staged (tuning)
 };
 
 // Physical parameters, with the derived constants the kernels use.

@@ -86,6 +86,31 @@ def test_adjoint_step_parity(case, prec):
     sim.close()
 
 
+@pytest.mark.parametrize("mode", ["0", "1", "2"])
+@pytest.mark.parametrize("case", [CASES[2], CASES[4], dict(nx=70, ny=40, nz=33, xbc=1, solid=((30, 20, 16), (31, 20, 16)))],
+                         ids=["inflow", "ragged", "multi_sweep"])
+def test_fp32_adjoint_kernels(case, mode, monkeypatch):
+    """The three FP32 adjoint kernels (one cell per thread, persistent,
+    persistent shared-memory staged; RLB_ADJ_PIPE) against the oracle; the
+    last lattice (92400 cells) needs more than one sweep of the persistent
+    grids over the cells."""
+    monkeypatch.setenv("RLB_ADJ_PIPE", mode)
+    w, p, sim, st, gstate, rng = _setup(case, "fp32", 13)
+    lam_in = rng.normal(size=st.shape).astype(np.float32).astype(np.float64)
+    ref_out, ref_dtau, ref_db = oracle.adjoint_step(p, st, lam_in, w.solid)
+    li = sim.cells_to_state(torch.from_numpy(lam_in).cuda())
+    lo = torch.full_like(li, float("nan"))
+    acc = torch.zeros(4, dtype=torch.float64, device="cuda")
+    sim.adjoint_step(gstate, li, lo, acc[0:1], acc[1:4])
+    got = sim.state_to_cells(lo).double().cpu().numpy()
+    assert not np.isnan(got).any()
+    assert _rel(got, ref_out) <= TOL["fp32"]
+    a = acc.cpu().numpy()
+    assert abs(a[0] - ref_dtau) <= TOL["fp32"] * max(abs(ref_dtau), 1e-12) * 10
+    assert np.max(np.abs(a[1:] - ref_db)) <= TOL["fp32"] * max(np.max(np.abs(ref_db)), 1e-12) * 10
+    sim.close()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("case", CASES[:3], ids=IDS[:3])
 def test_adjoint_macro_and_fields_parity(case, prec):
