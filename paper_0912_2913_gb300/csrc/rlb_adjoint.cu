@@ -250,6 +250,30 @@ static AdjConst<T> make_adj_const(const Phys& ph) {
     return c;
 }
 
+// Sums over the 19 populations as shallow trees (independent partial sums
+// instead of one 18-deep dependency chain).
+template <typename T>
+__device__ __forceinline__ T sum19(const T* h) {
+    const T a0 = h[0] + h[1], a1 = h[2] + h[3], a2 = h[4] + h[5], a3 = h[6] + h[7], a4 = h[8] + h[9];
+    const T a5 = h[10] + h[11], a6 = h[12] + h[13], a7 = h[14] + h[15], a8 = h[16] + h[17];
+    return ((a0 + a1) + (a2 + a3)) + (((a4 + a5) + (a6 + a7)) + (a8 + h[18]));
+}
+template <typename T>
+__device__ __forceinline__ T dot19(const T* a, const T* b) {
+    T s0 = a[0] * b[0], s1 = a[1] * b[1], s2 = a[2] * b[2], s3 = a[3] * b[3];
+#pragma unroll
+    for (int i = 4; i < 16; i += 4) {
+        s0 += a[i] * b[i];
+        s1 += a[i + 1] * b[i + 1];
+        s2 += a[i + 2] * b[i + 2];
+        s3 += a[i + 3] * b[i + 3];
+    }
+    s0 += a[16] * b[16];
+    s1 += a[17] * b[17];
+    s2 += a[18] * b[18];
+    return (s0 + s1) + (s2 + s3);
+}
+
 // What the g phase leaves for the f phase and the recovery adjoint.
 template <typename T>
 struct CellG {
@@ -261,12 +285,10 @@ struct CellG {
 // collision adjoint at mu = mug.
 template <typename T>
 __device__ __forceinline__ void cell_g(const T* h, const T* mug, const AdjConst<T>& c, CellG<T>& r) {
-    T dE = h[0], dd[9];
+    const T dE = sum19(h);
+    T dd[9];
 #pragma unroll
-    for (int p = 0; p < 9; ++p) {
-        dE += h[2 * p + 1] + h[2 * p + 2];
-        dd[p] = h[2 * p + 1] - h[2 * p + 2];
-    }
+    for (int p = 0; p < 9; ++p) dd[p] = h[2 * p + 1] - h[2 * p + 2];
     const T mx = c.c_l * (dd[0] + dd[3] + dd[4] + dd[5] + dd[6]);
     const T my = c.c_l * (dd[1] + dd[3] - dd[4] + dd[7] + dd[8]);
     const T mz = c.c_l * (dd[2] + dd[5] - dd[6] + dd[7] - dd[8]);
@@ -322,9 +344,7 @@ __device__ __forceinline__ void cell_g(const T* h, const T* mug, const AdjConst<
     //   d/d gamma^2 = eps (SYM + ASY + rest term), d/d b2 = -2 eps gamma^2 (S1 + w0 mu_0)/c_l^2,
     //   d/d beta = eps gamma^2 (12 Vq / c_l^2 + 4 Vd / c_l) + (chain through gamma^2 and b2) beta,
     // SYM = (6 Sq2 - 2 b2 S1)/c_l^2, ASY = 4 Sdq / c_l; and likewise for f.
-    T muh = mug[0] * h[0];
-#pragma unroll
-    for (int i = 1; i < 19; ++i) muh += mug[i] * h[i];
+    const T muh = dot19(mug, h);
     T S1 = 0, Sq2 = 0, Sdq = 0, Vq[3] = {0, 0, 0}, Vd[3] = {0, 0, 0};
 #pragma unroll
     for (int p = 0; p < 9; ++p) {
@@ -373,13 +393,9 @@ template <typename T>
 __device__ __forceinline__ void cell_f(const T* h, const T* muf, const CellG<T>& r, const AdjConst<T>& c, T& tacc,
                                        T& aS, T& fbx, T& fby, T& fbz) {
     const T q[9] = {r.bx, r.by, r.bz, r.bx + r.by, r.bx - r.by, r.bx + r.bz, r.bx - r.bz, r.by + r.bz, r.by - r.bz};
-    T dS = h[0];
-#pragma unroll
-    for (int i = 1; i < 19; ++i) dS += h[i];
+    const T dS = sum19(h);
     const T Sfull = (sizeof(T) == 8) ? dS : dS + c.n_ref;
-    T muh = muf[0] * h[0];
-#pragma unroll
-    for (int i = 1; i < 19; ++i) muh += muf[i] * h[i];
+    const T muh = dot19(muf, h);
     T F1 = 0, Fdq = 0, Vf[3] = {0, 0, 0};
 #pragma unroll
     for (int p = 0; p < 9; ++p) {
@@ -531,10 +547,7 @@ __global__ void __launch_bounds__(128, MINB)
         {
             // a pulled solid marker is a NaN: test the per-value markers only
             // when the sum of the gathered values is NaN
-            T sum = h[0];
-#pragma unroll
-            for (int i = 1; i < 19; ++i) sum += h[i];
-            if (isnan(sum)) {
+            if (isnan(sum19(h))) {
 #pragma unroll
                 for (int i = 1; i < 19; ++i) {
                     if (is_solid(h[i])) {
@@ -601,20 +614,21 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-template <int XBC>
+// I: index type of the element offsets, int when 38 S < 2^31 (fewer address
+// instructions), else long long.
+template <int XBC, typename I>
 __global__ void __launch_bounds__(kStageThreads, 3)
     k_adjoint_step_staged(const float* __restrict__ A, const float* __restrict__ Lin, float* __restrict__ Lout,
                           Geom g, Phys ph, AdjConst<float> c, double* red, const double* __restrict__ inflow_d) {
     extern __shared__ float stage[];  // [slot][value 0..37][thread]
-    const long long S = g.S;
+    const I S = (I)g.S;
     const int tid = threadIdx.x;
     const int stride = gridDim.x * blockDim.x;
     const uint32_t scol = (uint32_t)__cvta_generic_to_shared(stage) + 4u * tid;
     auto sval = [&](int slot, int q) -> float { return stage[(slot * 38 + q) * kStageThreads + tid]; };
     auto is_ghost = [&](int x) { return XBC != XBC_PERIODIC && (x == 0 || x == g.nx - 1); };
-    // one phase (base 19: g, base 0: f) of the cell at (x, y, z) into a slot
-    auto issue = [&](int cidx, int x, int y, int z, int base, int slot) {
-        const PullOffsets o(g, x, y, z);
+    // one phase (base 19: g, base 0: f) of a cell (pull offsets o) into a slot
+    auto issue = [&](int cidx, const PullOffsets& o, int base, int slot) {
         const uint32_t s0 = scol + 4u * (uint32_t)(slot * 38 * kStageThreads);
 #pragma unroll
         for (int i = 0; i < 19; ++i)
@@ -629,9 +643,11 @@ __global__ void __launch_bounds__(kStageThreads, 3)
     bool has_b = false;
     int idx = blockIdx.x * blockDim.x + tid;
     int x = 0, y = 0, z = 0;
+    PullOffsets o{};
     if (idx < g.N) {
         cell_coords(g, idx, x, y, z);
-        if (!is_ghost(x)) issue(idx, x, y, z, 19, 0);
+        o = PullOffsets(g, x, y, z);
+        if (!is_ghost(x)) issue(idx, o, 19, 0);
     }
     cp_async_commit();
     int sg = 0;
@@ -639,11 +655,15 @@ __global__ void __launch_bounds__(kStageThreads, 3)
         const int sf = sg == kStageSlots - 1 ? 0 : sg + 1;
         const int sn = sf == kStageSlots - 1 ? 0 : sf + 1;
         const bool ghost = is_ghost(x);
-        if (!ghost) issue(idx, x, y, z, 0, sf);
+        if (!ghost) issue(idx, o, 0, sf);
         cp_async_commit();
         const int nidx = idx + stride;
         int xn = 0, yn = 0, zn = 0;
-        if (nidx < g.N) cell_coords(g, nidx, xn, yn, zn);
+        PullOffsets on{};
+        if (nidx < g.N) {
+            cell_coords(g, nidx, xn, yn, zn);
+            on = PullOffsets(g, xn, yn, zn);
+        }
         cp_async_wait<1>();  // G_k has landed
         // ---- g phase
         unsigned bounced = 0u;
@@ -657,10 +677,7 @@ __global__ void __launch_bounds__(kStageThreads, 3)
             for (int i = 0; i < 19; ++i) h[i] = sval(sg, i);
             solid = is_solid(h[0]);  // the cell's own g_0 (pull offset 0)
             if (!solid) {
-                float sum = h[0];
-#pragma unroll
-                for (int i = 1; i < 19; ++i) sum += h[i];
-                if (isnan(sum)) {
+                if (isnan(sum19(h))) {
 #pragma unroll
                     for (int i = 1; i < 19; ++i) {
                         if (is_solid(h[i])) {
@@ -678,7 +695,7 @@ __global__ void __launch_bounds__(kStageThreads, 3)
                 cell_g(h, mug, c, r);
             }
         }
-        if (nidx < g.N && !is_ghost(xn)) issue(nidx, xn, yn, zn, 19, sn);
+        if (nidx < g.N && !is_ghost(xn)) issue(nidx, on, 19, sn);
         cp_async_commit();
         cp_async_wait<1>();  // F_k has landed
         // ---- f phase, scatter
@@ -691,7 +708,6 @@ __global__ void __launch_bounds__(kStageThreads, 3)
                 Lout[(19 + i) * S + idx] = sval(sg, 19 + i);
             }
         } else {
-            const PullOffsets o(g, x, y, z);
             float h[19], muf[19];
 #pragma unroll
             for (int i = 0; i < 19; ++i) h[i] = sval(sf, i);
@@ -722,8 +738,7 @@ __global__ void __launch_bounds__(kStageThreads, 3)
         }
         sg = sn;
         x = xn;
-        y = yn;
-        z = zn;
+        o = on;
     }
     cp_async_wait<0>();
     warp_partials<float>((double)tau_acc, bin0, bin1, bin2, has_b, red);
@@ -881,23 +896,32 @@ static int adjoint_step_t(const Geom& g, const Phys& ph, const T* A, const T* Li
     int grid = nb;
     if constexpr (sizeof(T) == 4) {
         if (g.adj_pipe == 2) {
+            const bool idx32 = !g.adj_idx64 && 38 * g.S < (1ll << 31);
             auto staged = [&](auto kern) {
                 // the shared-memory opt-in, once per device and kernel
-                static unsigned char attr[64][3];
+                static unsigned char attr[64][6];
+                const int which = g.xbc + (idx32 ? 0 : 3);
                 int dev = 0;
                 cudaGetDevice(&dev);
-                if (dev >= 0 && dev < 64 && !attr[dev][g.xbc]) {
+                if (dev >= 0 && dev < 64 && !attr[dev][which]) {
                     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageSmemBytes);
-                    attr[dev][g.xbc] = 1;
+                    attr[dev][which] = 1;
                 }
                 const int grid = persistent_grid(3);
                 kern<<<grid, kStageThreads, kStageSmemBytes, st>>>(A, Li, Lo, g, ph, c, red, inflow_d);
                 return grid;
             };
+            if (idx32) {
+                switch (g.xbc) {
+                    case XBC_PERIODIC: return staged(k_adjoint_step_staged<XBC_PERIODIC, int>);
+                    case XBC_INFLOW_OUTFLOW: return staged(k_adjoint_step_staged<XBC_INFLOW_OUTFLOW, int>);
+                    default: return staged(k_adjoint_step_staged<XBC_OUTFLOW_BOTH, int>);
+                }
+            }
             switch (g.xbc) {
-                case XBC_PERIODIC: return staged(k_adjoint_step_staged<XBC_PERIODIC>);
-                case XBC_INFLOW_OUTFLOW: return staged(k_adjoint_step_staged<XBC_INFLOW_OUTFLOW>);
-                default: return staged(k_adjoint_step_staged<XBC_OUTFLOW_BOTH>);
+                case XBC_PERIODIC: return staged(k_adjoint_step_staged<XBC_PERIODIC, long long>);
+                case XBC_INFLOW_OUTFLOW: return staged(k_adjoint_step_staged<XBC_INFLOW_OUTFLOW, long long>);
+                default: return staged(k_adjoint_step_staged<XBC_OUTFLOW_BOTH, long long>);
             }
         }
     }

@@ -115,6 +115,7 @@ __device__ __forceinline__ float d2f_seed(double d) {
 struct PullOffsets {
     int xm, xp, ym, yp, zm, zp;  // source at x-1 / x+1, y-1 / y+1, z-1 / z+1
 
+    PullOffsets() = default;
     __device__ __forceinline__ PullOffsets(const Geom& g, int x, int y, int z) {
         xm = (x == 0) ? g.nx - 1 : -1;
         xp = (x == g.nx - 1) ? -(g.nx - 1) : 1;

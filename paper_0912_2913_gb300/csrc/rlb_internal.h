@@ -39,6 +39,7 @@ struct Geom {
     int pipe_blocks;  // resident blocks per SM of the persistent variant (tuning)
     FastDiv div_nx, div_ny;
     int adj_pipe;  // FP32 adjoint kernel: 0 one cell per thread, 1 persistent, 2 staged (tuning)
+    int adj_idx64;  // 1: 64-bit element offsets in the staged adjoint even where 32 bits suffice (testing)
 };
 
 // Physical parameters, with the derived constants the kernels use.
