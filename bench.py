@@ -284,7 +284,8 @@ def e2e_run(w, job_steps, jobs, device):
 
 
 def traffic_from_profiles(kernel: str, digest: str, workload: str):
-    """DRAM bytes per launch from a committed ncu summary, if taken on this build."""
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current inputs of the kernel's translation unit."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
@@ -384,7 +385,8 @@ def run_ours(args):
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
-                         "traffic": traffic_from_profiles(kern, B._digest(), args.workload), "kernel": kern,
+                         "traffic": traffic_from_profiles(kern, B.unit_digest("rlb_forward.cu"), args.workload),
+                         "kernel": kern,
                          "bytes_per_launch": BYTES_FWD["fp32"] * w.N},
             "legs": legs,
             "clocks": clocks,

@@ -25,8 +25,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # results do not depend on launch variant or register allocation.
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC", "-Xcompiler",
               "-fvisibility=hidden", "--expt-relaxed-constexpr"]
-# The adjoint kernels run in one launch configuration, so contraction there
-# cannot make results depend on the launch; it is allowed for speed.
+# The adjoint kernels are held to the oracle within a tolerance rather than
+# bit for bit across launch variants, so contraction is allowed there for speed.
 FMAD_SOURCES = {"rlb_adjoint.cu"}
 
 
@@ -45,6 +45,19 @@ def _digest() -> str:
     with open(os.path.join(INCLUDE, "rlb.h"), "rb") as fh:
         h.update(fh.read())
     h.update(" ".join(ARCH + NVCC_FLAGS + sorted(FMAD_SOURCES)).encode())
+    return h.hexdigest()[:12]
+
+
+def unit_digest(source: str) -> str:
+    """Digest of what one translation unit is compiled from (the .cu file,
+    the shared headers and the flags): the kernels it defines change only if
+    this does."""
+    h = hashlib.sha1()
+    for name in [source] + HEADERS:
+        with open(os.path.join(CSRC, name), "rb") as fh:
+            h.update(fh.read())
+    flags = ARCH + NVCC_FLAGS + (["-fmad=true"] if source in FMAD_SOURCES else [])
+    h.update(" ".join(flags).encode())
     return h.hexdigest()[:12]
 
 

@@ -182,9 +182,18 @@ __global__ void __launch_bounds__(1024) k_finalize(const double* __restrict__ re
                                                    double* dbeta_in) {
     __shared__ double sm[4][256];
     const int k = threadIdx.x >> 8, t = threadIdx.x & 255;
-    double acc = 0.0;
-    for (int b = t; b < nblocks; b += 256) acc += red[b * 4 + k];
-    sm[k][t] = acc;
+    // eight independent partial sums so that eight loads are in flight; the
+    // grouping depends only on nblocks (deterministic)
+    double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int b = t;
+    for (; b + 7 * 256 < nblocks; b += 8 * 256) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) a[j] += red[(b + j * 256) * 4 + k];
+    }
+#pragma unroll
+    for (int j = 0; j < 7; ++j)
+        if (b + j * 256 < nblocks) a[j] += red[(b + j * 256) * 4 + k];
+    sm[k][t] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
     __syncthreads();
     for (int h = 128; h > 0; h >>= 1) {
         if (t < h) sm[k][t] += sm[k][t + h];
