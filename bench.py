@@ -264,7 +264,7 @@ def e2e_run(w, job_steps, jobs, device):
     hn = torch.from_numpy(np.ascontiguousarray(w.n)).pin_memory().numpy()
     he = torch.from_numpy(np.ascontiguousarray(w.eps)).pin_memory().numpy()
     hb = torch.from_numpy(np.ascontiguousarray(w.beta)).pin_memory().numpy()
-    hs = torch.from_numpy(np.ascontiguousarray(w.solid)).pin_memory().numpy()
+    hs = None if w.solid is None else torch.from_numpy(np.ascontiguousarray(w.solid)).pin_memory().numpy()
     sim.init_fields(hn, he, hb, hs).step(20)
     sim.macro(where="host")
     torch.cuda.synchronize()
@@ -276,7 +276,7 @@ def e2e_run(w, job_steps, jobs, device):
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     sim.close()
-    bi = hn.nbytes + he.nbytes + hb.nbytes + hs.nbytes
+    bi = hn.nbytes + he.nbytes + hb.nbytes + (0 if hs is None else hs.nbytes)
     bo = out[0].nbytes + out[1].nbytes + out[2].nbytes
     return {"value": w.N * job_steps * jobs / dt / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": bi / job_steps,
             "d2h_bytes_per_step": bo / job_steps,
