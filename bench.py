@@ -249,8 +249,83 @@ def cpu_baseline(w, budget_s=12.0):
         if time.time() - t0 > budget_s and k >= 2:
             break
     dt = time.time() - t0
-    return {"value": w.N * k / dt / 1e6, "unit": "MLUPS", "cores": oracle.get_threads(), "kind": "oracle",
-            "sample": f"{k} FP64 oracle steps of the full {w.nx}x{w.ny}x{w.nz} sphere lattice ({dt:.1f} s)"}
+    out = {"value": w.N * k / dt / 1e6, "unit": "MLUPS", "cores": oracle.get_threads(), "kind": "oracle",
+           "sample": f"{k} FP64 oracle steps of the full {w.nx}x{w.ny}x{w.nz} sphere lattice ({dt:.1f} s)"}
+    out["detail"] = oracle_thread_scaling(w)
+    return out
+
+
+def _oracle_mlups(p, st, solid, N, budget_s, min_steps):
+    import oracle
+
+    oracle.run(p, st, 1, solid=solid)
+    t0 = time.time()
+    k = 0
+    while True:
+        oracle.run(p, st, min_steps, solid=solid)
+        k += min_steps
+        if time.time() - t0 > budget_s:
+            break
+    return N * k / (time.time() - t0) / 1e6, k
+
+
+def oracle_thread_scaling(w, budget_s=2.0):
+    """The oracle at one thread and at all host cores on the 1D shock tube
+    (1600 cells) and on the given 3D workload, MLUPS (bounded samples)."""
+    import oracle
+
+    import workloads as W
+
+    nthr = oracle.get_threads()
+    res = {"cores": nthr}
+    tube = W.shock_tube_1d()
+    for name, wl, ms in (("shock_tube_1600", tube, 50), (f"{w.name}_{w.nx}x{w.ny}x{w.nz}", w, 1)):
+        p = oracle.Params(**wl.params())
+        for label, t in (("threads_1", 1), ("threads_all", nthr)):
+            oracle.set_threads(t)
+            st = oracle.init(p, wl.n, wl.eps, wl.beta, wl.solid)
+            v, k = _oracle_mlups(p, st, wl.solid, wl.N, budget_s, ms)
+            res.setdefault(name, {})[label] = {"mlups": v, "steps": k}
+    oracle.set_threads(nthr)
+    return res
+
+
+def shock_tube_graph_leg(device, steps_per_graph=100, replays=20):
+    """The launch-bound 1D shock tube (1600 cells, FP64): microseconds per step
+    with one rlb_step call per 1000 steps, and with steps_per_graph steps
+    captured once in a CUDA graph and replayed."""
+    import torch
+
+    import workloads as W
+    from paper_0912_2913_gb300 import RLB
+
+    w = W.shock_tube_1d()
+    s = torch.cuda.Stream(device=device)
+    sim = RLB.from_workload(w, "fp64", device=device, stream=s).init_fields(w.n, w.eps, w.beta)
+    sim.step(10)
+    torch.cuda.synchronize()
+    a, b = _events(torch, s)
+    a.record(s)
+    sim.step(1000)
+    b.record(s)
+    torch.cuda.synchronize()
+    us_plain = a.elapsed_time(b) * 1e3 / 1000
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        sim.step(steps_per_graph)
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    a.record(s)
+    for _ in range(replays):
+        g.replay()
+    b.record(s)
+    torch.cuda.synchronize()
+    us_graph = a.elapsed_time(b) * 1e3 / (replays * steps_per_graph)
+    sim.close()
+    return {"workload": "shock tube 1600x1x1 FP64, outflow ghosts at both ends", "us_per_step_stream": us_plain,
+            "us_per_step_graph": us_graph, "steps_per_graph": steps_per_graph,
+            "mlups_graph": w.N / us_graph}
 
 
 def e2e_run(w, job_steps, jobs, device):
@@ -364,6 +439,7 @@ def run_ours(args):
                 legs["fp64_adjoint"] = _leg(w, ms_all, ka, BYTES_ADJ["fp64"] + BYTES_FWD["fp64"], peak,
                                             {"adjoint_kernel_ms": ms_k / ka,
                                              "ratio_to_forward": (ms_all / ka) / (ms64 / k64)})
+            legs["shock_tube_fp64"] = shock_tube_graph_leg(device)
         sim.close()
         del sim
         torch.cuda.empty_cache()
