@@ -313,13 +313,14 @@ def shock_tube_graph_leg(device, steps_per_graph=100, replays=20):
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=s):
         sim.step(steps_per_graph)
-    for _ in range(2):
-        g.replay()
-    torch.cuda.synchronize()
-    a.record(s)
-    for _ in range(replays):
-        g.replay()
-    b.record(s)
+    with torch.cuda.stream(s):  # replay() launches on the current stream
+        for _ in range(2):
+            g.replay()
+        torch.cuda.synchronize()
+        a.record(s)
+        for _ in range(replays):
+            g.replay()
+        b.record(s)
     torch.cuda.synchronize()
     us_graph = a.elapsed_time(b) * 1e3 / (replays * steps_per_graph)
     sim.close()

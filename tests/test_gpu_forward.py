@@ -234,6 +234,34 @@ def test_tma_staged_step_equals_plain_step(shape, monkeypatch):
         assert states[0][1] == stats
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_cuda_graph_of_steps_matches_stream_steps(prec):
+    """rlb_step captured in a CUDA graph (an even number of steps, so the
+    ping-pong buffers return to their places) and replayed gives the state of
+    the same number of steps issued on the stream, bit for bit."""
+    from paper_0912_2913_gb300 import RLB
+
+    w = W.shock_tube_1d()
+    ref = RLB.from_workload(w, prec, device="cuda:0").init_fields(w.n, w.eps, w.beta)
+    ref.step(2).step(200)
+    s = torch.cuda.Stream()
+    sim = RLB.from_workload(w, prec, device="cuda:0", stream=s).init_fields(w.n, w.eps, w.beta)
+    sim.step(2)  # the first FP32 step times its launch variants: not in a capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        sim.step(100)
+    with torch.cuda.stream(s):
+        g.replay()
+        g.replay()
+    torch.cuda.synchronize()
+    a, b = ref.state()[:, :w.N].clone(), sim.state()[:, :w.N].clone()
+    iv = torch.int64 if prec == "fp64" else torch.int32
+    assert torch.equal(a.view(iv), b.view(iv))
+    ref.close()
+    sim.close()
+
+
 def test_step_into_matches_step():
     w = tiny_workload(12, 6, 5, 1, seed=5, solid_cells=((5, 3, 2),))
     from paper_0912_2913_gb300 import RLB
