@@ -466,33 +466,45 @@ cudaError_t launch_init(int prec, const Geom& g, const Phys& ph, const double* n
     return cudaGetLastError();
 }
 
+static int sm_count() {
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    }
+    return nsm;
+}
+
+// Threads per block of the one-cell-per-thread step kernels: a lattice with
+// fewer blocks than SMs (the 1600-cell shock tube) runs 32-thread blocks, so
+// that its cells spread over up to 32x more SMs (the per-cell arithmetic,
+// FP64 above all, is then the step's latency).  Results do not depend on it.
+static int step_block(long long N, int full) { return blocks_for(N, full) < (unsigned)sm_count() ? 32 : full; }
+
 template <int XBC, bool SOLID>
 static void launch_step_t(int prec, const Geom& g, const Phys& ph, const void* A, void* B, Counters cnt, bool count,
                           long long step_index, cudaStream_t st) {
     if (prec == 0) {
-        k_step_f64<XBC, SOLID><<<blocks_for(g.N, 128), 128, 0, st>>>((const double*)A, (double*)B, g, ph, cnt,
-                                                                      count ? 1 : 0, step_index);
+        const int tb = step_block(g.N, 128);
+        k_step_f64<XBC, SOLID><<<blocks_for(g.N, tb), tb, 0, st>>>((const double*)A, (double*)B, g, ph, cnt,
+                                                                    count ? 1 : 0, step_index);
     } else {
         const Dev32 c = make_dev32(ph);
         if (g.tma && launch_step_f32_tma(g, c, (const float*)A, (float*)B, cnt, count, step_index, st) == cudaSuccess)
             return;
         cudaGetLastError();
-        const unsigned nb = blocks_for(g.N, 256);
+        const int tb = step_block(g.N, 256);
+        const unsigned nb = blocks_for(g.N, tb);
         const int cs = count ? 1 : 0;
         switch (g.variant) {
-            case 0: k_step_f32<XBC, SOLID, 3, false><<<nb, 256, 0, st>>>((const float*)A, (float*)B, g, c, cnt, cs, step_index); break;
-            case 1: k_step_f32<XBC, SOLID, 3, true><<<nb, 256, 0, st>>>((const float*)A, (float*)B, g, c, cnt, cs, step_index); break;
-            case 2: k_step_f32<XBC, SOLID, 4, false><<<nb, 256, 0, st>>>((const float*)A, (float*)B, g, c, cnt, cs, step_index); break;
-            case 3: k_step_f32<XBC, SOLID, 4, true><<<nb, 256, 0, st>>>((const float*)A, (float*)B, g, c, cnt, cs, step_index); break;
+            case 0: k_step_f32<XBC, SOLID, 3, false><<<nb, tb, 0, st>>>((const float*)A, (float*)B, g, c, cnt, cs, step_index); break;
+            case 1: k_step_f32<XBC, SOLID, 3, true><<<nb, tb, 0, st>>>((const float*)A, (float*)B, g, c, cnt, cs, step_index); break;
+            case 2: k_step_f32<XBC, SOLID, 4, false><<<nb, tb, 0, st>>>((const float*)A, (float*)B, g, c, cnt, cs, step_index); break;
+            case 3: k_step_f32<XBC, SOLID, 4, true><<<nb, tb, 0, st>>>((const float*)A, (float*)B, g, c, cnt, cs, step_index); break;
             case 4:
             case 5: {
-                static int nsm = 0;
-                if (nsm == 0) {
-                    int dev = 0;
-                    cudaGetDevice(&dev);
-                    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-                }
-                unsigned grid = (unsigned)nsm * (unsigned)(g.pipe_blocks > 0 ? g.pipe_blocks : 3);
+                unsigned grid = (unsigned)sm_count() * (unsigned)(g.pipe_blocks > 0 ? g.pipe_blocks : 3);
                 if (grid > nb) grid = nb;
                 if (g.variant == 4)
                     k_step_f32_pipe<XBC, SOLID, false><<<grid, 256, 0, st>>>((const float*)A, (float*)B, g, c, cnt, cs, step_index);
@@ -500,7 +512,7 @@ static void launch_step_t(int prec, const Geom& g, const Phys& ph, const void* A
                     k_step_f32_pipe<XBC, SOLID, true><<<grid, 256, 0, st>>>((const float*)A, (float*)B, g, c, cnt, cs, step_index);
                 break;
             }
-            default: k_step_f32<XBC, SOLID, 3, true><<<nb, 256, 0, st>>>((const float*)A, (float*)B, g, c, cnt, cs, step_index); break;
+            default: k_step_f32<XBC, SOLID, 3, true><<<nb, tb, 0, st>>>((const float*)A, (float*)B, g, c, cnt, cs, step_index); break;
         }
     }
 }
