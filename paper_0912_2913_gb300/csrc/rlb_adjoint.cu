@@ -175,24 +175,25 @@ __device__ __forceinline__ void block_reduce4(double v0, double v1, double v2, d
     }
 }
 
-// Sum the per-block partials and add them to the accumulators.  256 threads
-// per component; thread t sums blocks t, t+256, ... in order, then a fixed
-// tree combines the 256 sums: the result does not depend on scheduling.
-__global__ void __launch_bounds__(1024) k_finalize(const double* __restrict__ red, int nblocks, double* dtau,
+// Sum the partial-sum slots (one per warp or per block, 4 doubles each) and
+// add them to the accumulators.  256 threads per component; thread t sums
+// slots t, t+256, ... in a fixed grouping, then a fixed tree combines the 256
+// sums: the result does not depend on scheduling.
+__global__ void __launch_bounds__(1024) k_finalize(const double* __restrict__ red, int nslots, double* dtau,
                                                    double* dbeta_in) {
     __shared__ double sm[4][256];
     const int k = threadIdx.x >> 8, t = threadIdx.x & 255;
     // eight independent partial sums so that eight loads are in flight; the
-    // grouping depends only on nblocks (deterministic)
+    // grouping depends only on nslots (deterministic)
     double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     int b = t;
-    for (; b + 7 * 256 < nblocks; b += 8 * 256) {
+    for (; b + 7 * 256 < nslots; b += 8 * 256) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) a[j] += red[(b + j * 256) * 4 + k];
     }
 #pragma unroll
     for (int j = 0; j < 7; ++j)
-        if (b + j * 256 < nblocks) a[j] += red[(b + j * 256) * 4 + k];
+        if (b + j * 256 < nslots) a[j] += red[(b + j * 256) * 4 + k];
     sm[k][t] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
     __syncthreads();
     for (int h = 128; h > 0; h >>= 1) {
@@ -897,12 +898,13 @@ static int adjoint_step_t(const Geom& g, const Phys& ph, const T* A, const T* Li
         const int pg = nsm * minb;
         return pg < nb ? pg : nb;
     };
+    // each launcher returns the number of warps whose partial sums it wrote
     auto go = [&](auto kern, bool pipe, int minb) {
         const int grid = pipe ? persistent_grid(minb) : nb;
         kern<<<grid, 128, 0, st>>>(A, Li, Lo, g, ph, c, red, inflow_d);
-        return grid;
+        return grid * 4;
     };
-    int grid = nb;
+    int warps = 0;
     if constexpr (sizeof(T) == 4) {
         if (g.adj_pipe == 2) {
             const bool idx32 = !g.adj_idx64 && 38 * g.S < (1ll << 31);
@@ -918,7 +920,7 @@ static int adjoint_step_t(const Geom& g, const Phys& ph, const T* A, const T* Li
                 }
                 const int grid = persistent_grid(3);
                 kern<<<grid, kStageThreads, kStageSmemBytes, st>>>(A, Li, Lo, g, ph, c, red, inflow_d);
-                return grid;
+                return grid * (kStageThreads / 32);
             };
             if (idx32) {
                 switch (g.xbc) {
@@ -936,24 +938,24 @@ static int adjoint_step_t(const Geom& g, const Phys& ph, const T* A, const T* Li
     }
     if constexpr (sizeof(T) == 8) {
         switch (g.xbc) {
-            case XBC_PERIODIC: grid = go(k_adjoint_step<T, XBC_PERIODIC, 2, false>, false, 2); break;
-            case XBC_INFLOW_OUTFLOW: grid = go(k_adjoint_step<T, XBC_INFLOW_OUTFLOW, 2, false>, false, 2); break;
-            default: grid = go(k_adjoint_step<T, XBC_OUTFLOW_BOTH, 2, false>, false, 2); break;
+            case XBC_PERIODIC: warps = go(k_adjoint_step<T, XBC_PERIODIC, 2, false>, false, 2); break;
+            case XBC_INFLOW_OUTFLOW: warps = go(k_adjoint_step<T, XBC_INFLOW_OUTFLOW, 2, false>, false, 2); break;
+            default: warps = go(k_adjoint_step<T, XBC_OUTFLOW_BOTH, 2, false>, false, 2); break;
         }
     } else if (g.adj_pipe) {
         switch (g.xbc) {
-            case XBC_PERIODIC: grid = go(k_adjoint_step<T, XBC_PERIODIC, 4, true>, true, 4); break;
-            case XBC_INFLOW_OUTFLOW: grid = go(k_adjoint_step<T, XBC_INFLOW_OUTFLOW, 4, true>, true, 4); break;
-            default: grid = go(k_adjoint_step<T, XBC_OUTFLOW_BOTH, 4, true>, true, 4); break;
+            case XBC_PERIODIC: warps = go(k_adjoint_step<T, XBC_PERIODIC, 4, true>, true, 4); break;
+            case XBC_INFLOW_OUTFLOW: warps = go(k_adjoint_step<T, XBC_INFLOW_OUTFLOW, 4, true>, true, 4); break;
+            default: warps = go(k_adjoint_step<T, XBC_OUTFLOW_BOTH, 4, true>, true, 4); break;
         }
     } else {
         switch (g.xbc) {
-            case XBC_PERIODIC: grid = go(k_adjoint_step<T, XBC_PERIODIC, 4, false>, false, 4); break;
-            case XBC_INFLOW_OUTFLOW: grid = go(k_adjoint_step<T, XBC_INFLOW_OUTFLOW, 4, false>, false, 4); break;
-            default: grid = go(k_adjoint_step<T, XBC_OUTFLOW_BOTH, 4, false>, false, 4); break;
+            case XBC_PERIODIC: warps = go(k_adjoint_step<T, XBC_PERIODIC, 4, false>, false, 4); break;
+            case XBC_INFLOW_OUTFLOW: warps = go(k_adjoint_step<T, XBC_INFLOW_OUTFLOW, 4, false>, false, 4); break;
+            default: warps = go(k_adjoint_step<T, XBC_OUTFLOW_BOTH, 4, false>, false, 4); break;
         }
     }
-    return grid;
+    return warps;
 }
 
 cudaError_t launch_adjoint_step(int prec, const Geom& g, const Phys& ph, const void* A, const void* lam_in,
@@ -961,14 +963,14 @@ cudaError_t launch_adjoint_step(int prec, const Geom& g, const Phys& ph, const v
                                 cudaStream_t st) {
     const int nb = adj_blocks(g.N);
     set_last_launch_count(2);
-    int grid;
+    int warps;
     if (prec == 0)
-        grid = adjoint_step_t<double>(g, ph, (const double*)A, (const double*)lam_in, (double*)lam_out, red, nb,
-                                      inflow_d, st);
+        warps = adjoint_step_t<double>(g, ph, (const double*)A, (const double*)lam_in, (double*)lam_out, red, nb,
+                                       inflow_d, st);
     else
-        grid = adjoint_step_t<float>(g, ph, (const float*)A, (const float*)lam_in, (float*)lam_out, red, nb, inflow_d,
-                                     st);
-    k_finalize<<<1, 1024, 0, st>>>(red, grid * 4, dtau, dbeta_in);
+        warps = adjoint_step_t<float>(g, ph, (const float*)A, (const float*)lam_in, (float*)lam_out, red, nb,
+                                      inflow_d, st);
+    k_finalize<<<1, 1024, 0, st>>>(red, warps, dtau, dbeta_in);
     return cudaGetLastError();
 }
 
