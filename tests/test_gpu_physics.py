@@ -1,0 +1,97 @@
+"""The paper's Riemann validations on the GPU path: the eta/s sweep of the
+beta ~ 0.2 case (LB side of Figs. 3-4; the BAMPS curves are not available)
+and the numerical-tachyon runs (c_l = 10) of Fig. 5 and of the 1:16 strong
+shock, against the oracle and the exact ideal Riemann solution."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+from oracle import riemann
+from paper_0912_2913_gb300 import physics as ph
+from tests._helpers import gpu_run, oracle_run, rel_errors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+
+
+def _xi(w):
+    return (np.arange(w.nx) + 0.5 - w.nx // 2) * w.c_l / w.steps
+
+
+def test_eta_over_s_sweep_beta02():
+    """tau from eta/s in the left initial state (5.43 GeV/fm^3, 350 MeV) for
+    eta/s = 0.01 ... 0.2, 400 steps (3.2 fm/c) on 800 cells, FP64: the run at
+    eta/s = 0.1 equals the oracle to 1e-10, and the L1 distance of the
+    pressure and velocity profiles from the ideal (eta = 0) solution grows
+    with eta/s."""
+    su = ph.paper_setup_beta02()
+    T = su.steps_for(3.2)
+    sol = riemann.solve(3 * su.P0, su.P0 / su.T0, 3 * su.P1, su.P1 / su.T1)
+    dists = []
+    for ratio in (0.01, 0.05, 0.1, 0.2):
+        tau = su.tau_for(ratio)
+        w = W.riemann_tube(su.P0, su.P1, su.T0, su.T1, cells=su.cells, tau=tau, c_l=su.c_l, steps=T)
+        got, sim = gpu_run(w, T, "fp64")
+        assert sim.stats()["n_unphysical"] == 0
+        sim.close()
+        if ratio == 0.1:
+            ref, _ = oracle_run(w, T)
+            assert max(rel_errors(got, ref)) <= 1e-10
+        n, e, b = got
+        ex, _, bex = sol.sample(_xi(w))
+        inner = slice(1, w.nx - 1)
+        dp = np.abs(e[0, 0, inner] - ex[inner]).mean() / (3 * su.P0)
+        db = np.abs(b[0, 0, 0, inner] - bex[inner]).mean()
+        dists.append((ratio, tau, dp, db))
+    for (_, _, dp0, db0), (_, _, dp1, db1) in zip(dists, dists[1:]):
+        assert dp1 > dp0 and db1 > db0, dists
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_tachyon_fig5_setup(prec):
+    """Fig. 5's parameters as given (c_l = 10, P1 = 0.9532 GeV/fm^3, T0 =
+    0.0328, T1 = 0.0164; P0 kept at 5.43 GeV/fm^3), eta/s = 0.01 and 0.001,
+    3.2 fm/c = 4000 steps: the LB star plateau matches the exact solution for
+    these inputs, beta* = 0.361 (not the caption's ~0.6: P0 of that run is not
+    given)."""
+    su = ph.paper_setup_tachyon()
+    T = su.steps_for(3.2)
+    sol = riemann.solve(3 * su.P0, su.P0 / su.T0, 3 * su.P1, su.P1 / su.T1)
+    assert sol.beta_star == pytest.approx(0.3610, abs=5e-4)
+    for ratio, tol in ((0.01, 5e-4), (0.001, 3e-3)):
+        w = W.riemann_tube(su.P0, su.P1, su.T0, su.T1, cells=su.cells, tau=su.tau_for(ratio), c_l=su.c_l, steps=T)
+        (n, e, b), sim = gpu_run(w, T, prec)
+        assert sim.stats()["n_unphysical"] == 0
+        sim.close()
+        xi = _xi(w)
+        plateau = (xi > sol.xi_tail + 0.05) & (xi < sol.v_shock - 0.05)
+        assert plateau.sum() > 150
+        assert abs(b[0, 0, 0][plateau].mean() / sol.beta_star - 1) < tol
+        assert abs(e[0, 0][plateau].mean() / sol.eps_star - 1) < tol
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_tachyon_strong_shock(prec):
+    """The 1:16 strong shock with c_l = 10 (within the positivity bound of the
+    f equilibria, beta* = 0.541), 1600 cells, 4000 steps at tau = 0.52: parity
+    with the oracle, and the star plateau against the exact solution."""
+    P0, T0, P1, T1 = 1 / 3, 1 / 3, 1 / 48, 1 / 6
+    w = W.riemann_tube(P0, P1, T0, T1, cells=1598, tau=0.52, c_l=10.0, steps=4000)
+    got, sim = gpu_run(w, w.steps, prec)
+    assert sim.stats()["n_unphysical"] == 0
+    sim.close()
+    ref, _ = oracle_run(w, w.steps)
+    assert max(rel_errors(got, ref)) <= (1e-10 if prec == "fp64" else 1e-4)
+    sol = riemann.solve(3 * P0, P0 / T0, 3 * P1, P1 / T1)
+    xi = _xi(w)
+    plateau = (xi > sol.xi_tail + 0.05) & (xi < sol.v_shock - 0.05)
+    n, e, b = got
+    assert abs(b[0, 0, 0][plateau].mean() - sol.beta_star) < 3e-4
+    assert abs(e[0, 0][plateau].mean() / sol.eps_star - 1) < 1e-3

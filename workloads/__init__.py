@@ -80,6 +80,20 @@ def shock_tube_1d(nx: int = 1600, tau: float = 0.9, steps: int = 2000, eps_l: fl
     return Workload("shock_tube_1d", nx, 1, 1, tau, c_l, XBC_OUTFLOW_BOTH, steps, n, eps, beta)
 
 
+def riemann_tube(P0: float, P1: float, T0: float, T1: float, cells: int = 800, tau: float = 0.52,
+                 c_l: float = 1.0, steps: int = 400) -> Workload:
+    """Riemann problem of two equilibrated half spaces at rest: pressure P0 and
+    temperature T0 left of the membrane, P1 and T1 right of it (eps = 3P,
+    n = P/T), cells interior cells plus an outflow ghost plane at each end."""
+    nx = cells + 2
+    x = np.arange(nx)
+    left = x < nx // 2
+    eps = np.where(left, 3.0 * P0, 3.0 * P1).astype(np.float64)[None, None, :]
+    n = np.where(left, P0 / T0, P1 / T1).astype(np.float64)[None, None, :]
+    beta = np.zeros((3, 1, 1, nx))
+    return Workload("riemann_tube", nx, 1, 1, tau, c_l, XBC_OUTFLOW_BOTH, steps, n, eps, beta)
+
+
 def perturbed_shock_tube(nx: int = 1600, tau: float = 0.9, steps: int = 2000, seed: int = 5,
                          amp: float = 0.05) -> Workload:
     w = shock_tube_1d(nx=nx, tau=tau, steps=steps)
