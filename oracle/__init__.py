@@ -28,6 +28,8 @@ _BUILD = os.path.join(_HERE, "_build")
 XBC_PERIODIC = 0
 XBC_INFLOW_OUTFLOW = 1
 XBC_OUTFLOW_BOTH = 2
+EOS_ULTRA = 0
+EOS_GAMMA_LAW = 1
 
 
 def _src_hash() -> str:
@@ -57,7 +59,9 @@ def build(force: bool = False) -> str:
 class _Params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
                 ("xbc", ctypes.c_int32), ("tau", ctypes.c_double), ("c_l", ctypes.c_double),
-                ("n_in", ctypes.c_double), ("eps_in", ctypes.c_double), ("beta_in", ctypes.c_double * 3)]
+                ("n_in", ctypes.c_double), ("eps_in", ctypes.c_double), ("beta_in", ctypes.c_double * 3),
+                ("eos", ctypes.c_int32), ("pad", ctypes.c_int32), ("eos_gamma", ctypes.c_double),
+                ("eos_mass", ctypes.c_double)]
 
 
 class _Stats(ctypes.Structure):
@@ -95,6 +99,13 @@ def lib():
         L.orc_collide.argtypes = [P(d), d, d, P(d)]
         L.orc_positivity_flag.argtypes = [P(d), d]
         L.orc_positivity_flag.restype = ctypes.c_int
+        L.orc_eos_pressure.argtypes = [d, d, d, d]
+        L.orc_eos_pressure.restype = d
+        L.orc_equilibrium_general.argtypes = [d, d, d, P(d), d, P(d), P(d)]
+        L.orc_recover_general.argtypes = [P(d), d, d, d, P(d), P(d), P(d), P(d), P(ctypes.c_int)]
+        L.orc_recover_general.restype = ctypes.c_int
+        for f in (L.orc_adjoint_step, L.orc_adjoint_macro, L.orc_adjoint_fields):
+            f.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -119,6 +130,9 @@ class Params:
     n_in: float = 1.0
     eps_in: float = 1.0
     beta_in: tuple = (0.0, 0.0, 0.0)
+    eos: int = EOS_ULTRA
+    eos_gamma: float = 4.0 / 3.0
+    eos_mass: float = 0.0
 
     @property
     def N(self) -> int:
@@ -130,6 +144,8 @@ class Params:
         p.tau, p.c_l, p.n_in, p.eps_in = self.tau, self.c_l, self.n_in, self.eps_in
         for a in range(3):
             p.beta_in[a] = float(self.beta_in[a])
+        p.eos, p.pad = int(self.eos), 0
+        p.eos_gamma, p.eos_mass = float(self.eos_gamma), float(self.eos_mass)
         return p
 
 
@@ -213,6 +229,31 @@ def deq_dfields(n, eps, beta, c_l):
     return out
 
 
+def eos_pressure(gamma_ad, mass, n, eps) -> float:
+    """P = (Gamma - 1)(eps - n m)."""
+    return float(lib().orc_eos_pressure(float(gamma_ad), float(mass), float(n), float(eps)))
+
+
+def equilibrium_general(n, eps, P, beta, c_l):
+    """Eqs. (equil1), (equil2a), (equil2b) at pressure P."""
+    f = np.zeros(19)
+    g = np.zeros(19)
+    b = _f64(beta)
+    lib().orc_equilibrium_general(float(n), float(eps), float(P), _dp(b), float(c_l), _dp(f), _dp(g))
+    return f, g
+
+
+def recover_general(m, c_l, gamma_ad, mass):
+    """(n, eps, P, beta, unphysical, newton_iterations) from the five moments."""
+    mm = _f64(m)
+    n, eps, P = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    it = ctypes.c_int()
+    b = np.zeros(3)
+    bad = lib().orc_recover_general(_dp(mm), float(c_l), float(gamma_ad), float(mass), ctypes.byref(n),
+                                    ctypes.byref(eps), ctypes.byref(P), _dp(b), ctypes.byref(it))
+    return n.value, eps.value, P.value, b, bool(bad), it.value
+
+
 def positivity_flag(beta, c_l) -> bool:
     b = _f64(beta)
     return bool(lib().orc_positivity_flag(_dp(b), float(c_l)))
@@ -279,7 +320,8 @@ def adjoint_step(p: Params, state_t, lam_in, solid=None):
     lo = np.empty_like(li)
     dtau = ctypes.c_double(0.0)
     db = np.zeros(3)
-    lib().orc_adjoint_step(ctypes.byref(p._c()), sp, _dp(a), _dp(li), _dp(lo), ctypes.byref(dtau), _dp(db))
+    if lib().orc_adjoint_step(ctypes.byref(p._c()), sp, _dp(a), _dp(li), _dp(lo), ctypes.byref(dtau), _dp(db)) != 0:
+        raise ValueError("the oracle adjoint covers the eps = 3P equation of state only")
     return lo, dtau.value, db
 
 
@@ -288,7 +330,8 @@ def adjoint_macro(p: Params, state, dn, deps, dbeta, solid=None):
     a = _f64(state)
     dn_, de_, db_ = _f64(dn).reshape(-1), _f64(deps).reshape(-1), _f64(dbeta).reshape(-1)
     lam = np.empty((p.nz, p.ny, p.nx, 2, 19))
-    lib().orc_adjoint_macro(ctypes.byref(p._c()), sp, _dp(a), _dp(dn_), _dp(de_), _dp(db_), _dp(lam))
+    if lib().orc_adjoint_macro(ctypes.byref(p._c()), sp, _dp(a), _dp(dn_), _dp(de_), _dp(db_), _dp(lam)) != 0:
+        raise ValueError("the oracle adjoint covers the eps = 3P equation of state only")
     return lam
 
 
@@ -301,6 +344,7 @@ def adjoint_fields(p: Params, n, eps, beta, lam0, solid=None):
     de = np.empty((p.nz, p.ny, p.nx))
     db = np.empty((3, p.nz, p.ny, p.nx))
     dbi = np.zeros(3)
-    lib().orc_adjoint_fields(ctypes.byref(p._c()), sp, _dp(n_), _dp(e_), _dp(b_), _dp(l0), _dp(dn), _dp(de),
-                             _dp(db), _dp(dbi))
+    if lib().orc_adjoint_fields(ctypes.byref(p._c()), sp, _dp(n_), _dp(e_), _dp(b_), _dp(l0), _dp(dn), _dp(de),
+                             _dp(db), _dp(dbi)) != 0:
+        raise ValueError("the oracle adjoint covers the eps = 3P equation of state only")
     return dn, de, db, dbi

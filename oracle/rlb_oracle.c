@@ -30,7 +30,11 @@
  *    copied from x = nx-2 after each step, or outflow copies at both ends;
  *    y and z are always periodic;
  *  - macroscopic recovery: the positive root of the quadratic obtained from
- *    the three moment constraints with eps = 3P (derived in orc_recover).
+ *    the three moment constraints with eps = 3P (derived in orc_recover);
+ *  - general equation of state (eos = 1): an ideal gas with rest mass,
+ *    P = (Gamma - 1)(eps - n m), with the equilibria of Eqs. (equil1),
+ *    (equil2a), (equil2b) and a Newton iteration on P for the recovery
+ *    (orc_recover_general).  Gamma = 4/3, m = 0 is the eps = 3P case.
  */
 #include <math.h>
 #include <stdint.h>
@@ -67,11 +71,15 @@ static int opposite(int i) {
 
 enum { XBC_PERIODIC = 0, XBC_INFLOW_OUTFLOW = 1, XBC_OUTFLOW_BOTH = 2 };
 
+enum { EOS_ULTRA = 0, EOS_GAMMA_LAW = 1 };
+
 typedef struct {
     int32_t nx, ny, nz;
     int32_t xbc;
     double tau, c_l;
     double n_in, eps_in, beta_in[3];
+    int32_t eos, pad;
+    double eos_gamma, eos_mass;
 } orc_params;
 
 typedef struct {
@@ -181,6 +189,112 @@ int orc_recover(const double* m, double c_l, double* n, double* eps, double* bet
     return bad;
 }
 
+/* ------------------------------------------------------------------------ */
+/* General equation of state (the macroscopic constraints after Fig. 2 and   */
+/* Eqs. equil1, equil2a, equil2b): an ideal gas with rest mass m,             */
+/*     P = (Gamma - 1) (eps - n m).                                           */
+/* ------------------------------------------------------------------------ */
+double orc_eos_pressure(double gamma_ad, double mass, double n, double eps) {
+    return (gamma_ad - 1.0) * (eps - n * mass);
+}
+
+/* Eqs. (equil1), (equil2a), (equil2b) with pressure P. */
+void orc_equilibrium_general(double n, double eps, double P, const double* beta, double c_l, double* feq,
+                             double* geq) {
+    double b2 = beta[0] * beta[0] + beta[1] * beta[1] + beta[2] * beta[2];
+    double gam2 = 1.0 / (1.0 - b2);
+    double gam = sqrt(gam2);
+    double cl2 = c_l * c_l;
+    double h = (eps + P) * gam2; /* (eps + P) gamma^2 */
+    for (int i = 0; i < Q; ++i) {
+        double cu = (EV[i][0] * beta[0] + EV[i][1] * beta[1] + EV[i][2] * beta[2]) * c_l; /* c_i . u */
+        double w = weight(i);
+        /* Eq. (equil1): f_i = w_i n gamma [1 + 3 (c_i.u)/c_l^2] */
+        feq[i] = w * n * gam * (1.0 + 3.0 * cu / cl2);
+        if (i == 0) {
+            /* Eq. (equil2b): g_0 = w_0 (eps+P) gamma^2 [3 - 3P(2 + c_l^2)/((P+eps) gamma^2 c_l^2)
+             *                                            - (3/2)|u|^2/c_l^2] */
+            geq[i] = w * h * (3.0 - 3.0 * P * (2.0 + cl2) / ((P + eps) * gam2 * cl2) - 1.5 * b2 / cl2);
+        } else {
+            /* Eq. (equil2a): g_i = w_i (eps+P) gamma^2 [3P/((P+eps) gamma^2 c_l^2) + 3 (c_i.u)/c_l^2
+             *                      + (9/2)(c_i.u)^2/c_l^4 - (3/2)|u|^2/c_l^2] */
+            geq[i] = w * h *
+                     (3.0 * P / ((P + eps) * gam2 * cl2) + 3.0 * cu / cl2 + 4.5 * cu * cu / (cl2 * cl2) -
+                      1.5 * b2 / cl2);
+        }
+    }
+}
+
+/* Recovery of n, eps, P, beta from the moments m = (n gamma, T^00, T^0i)
+ * with P = (Gamma - 1)(eps - n m).  The constraints give, for a trial P,
+ *     beta = T^0i / (T^00 + P),   eps = T^00 - |T^0i|^2 / (T^00 + P),
+ *     n = (n gamma) sqrt(1 - beta^2),
+ * and P solves r(P) = (Gamma - 1)(eps(P) - m n(P)) - P = 0 with
+ *     r'(P) = (Gamma - 1)(beta^2 - m n beta^2 / ((T^00 + P)(1 - beta^2))) - 1.
+ * Newton from P = (Gamma - 1)(T^00 - m n gamma) (the value at rest), raised
+ * above |T^0i| - T^00 so that |beta| < 1, until |dP| <= 1e-14 (P + T^00)
+ * (eps(P) is formed by cancellation at high |beta|, so the last steps move P
+ * by rounding noise of T^00; at most 100 iterations).  Returns 1 when the state is unphysical
+ * (n gamma <= 0, T^00 <= 0, no convergence, P <= 0, |beta| >= 1, a
+ * non-finite value); *iters receives the iteration count.                   */
+int orc_recover_general(const double* m, double c_l, double gamma_ad, double mass, double* n, double* eps,
+                        double* P, double* beta, int* iters) {
+    (void)c_l;
+    double D = m[0], E = m[1];
+    double M2 = m[2] * m[2] + m[3] * m[3] + m[4] * m[4];
+    double M = sqrt(M2);
+    double g1 = gamma_ad - 1.0;
+    double p = g1 * (E - mass * D);
+    double lo = M - E;
+    if (!(p > lo)) p = lo + 1e-3 * (E > 0.0 ? E : 1.0);
+    int it = 0, conv = 0;
+    for (it = 0; it < 100; ++it) {
+        double W = E + p;
+        double b2 = M2 / (W * W);
+        double nn = D * sqrt(1.0 - b2);
+        double ep = E - M2 / W;
+        double r = g1 * (ep - mass * nn) - p;
+        double dr = g1 * (b2 - mass * nn * b2 / (W * (1.0 - b2))) - 1.0;
+        double dp = -r / dr;
+        p = p + dp;
+        if (fabs(dp) <= 1e-14 * (fabs(p) + fabs(E))) {
+            conv = 1;
+            ++it;
+            break;
+        }
+    }
+    double W = E + p;
+    double b[3];
+    for (int a = 0; a < 3; ++a) b[a] = m[2 + a] / W;
+    double b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+    double nn = D * sqrt(1.0 - b2);
+    double ep = E - M2 / W;
+    *n = nn;
+    *eps = ep;
+    *P = p;
+    for (int a = 0; a < 3; ++a) beta[a] = b[a];
+    if (iters) *iters = it;
+    int bad = 0;
+    if (!(D > 0.0)) bad = 1;
+    if (!(E > 0.0)) bad = 1;
+    if (!conv) bad = 1;
+    if (!(p > 0.0)) bad = 1;
+    if (!(b2 < 1.0)) bad = 1;
+    if (!isfinite(nn) || !isfinite(ep) || !isfinite(p) || !isfinite(b[0]) || !isfinite(b[1]) || !isfinite(b[2]))
+        bad = 1;
+    return bad;
+}
+
+/* Equilibria of a cell's fields under the run's equation of state. */
+static void equilibrium_of(const orc_params* p, double n, double eps, const double* beta, double* feq,
+                           double* geq) {
+    if (p->eos == EOS_GAMMA_LAW)
+        orc_equilibrium_general(n, eps, orc_eos_pressure(p->eos_gamma, p->eos_mass, n, eps), beta, p->c_l, feq,
+                                geq);
+    else
+        orc_equilibrium(n, eps, beta, p->c_l, feq, geq);
+}
+
 /* Positivity diagnostic (the condition stated after the tachyon paragraph:
  * f_i^eq > 0 requires c_i . u < c_l^2/3).  The decision is taken in binary32
  * on beta rounded to binary32, as the CUDA kernels take it:
@@ -248,9 +362,9 @@ int orc_init(const orc_params* p, const double* n, const double* eps, const doub
         int x = (int)(c % p->nx);
         double* h = state + c * NPOP;
         if (p->xbc == XBC_INFLOW_OUTFLOW && x == 0)
-            orc_equilibrium(p->n_in, p->eps_in, p->beta_in, p->c_l, h, h + Q);
+            equilibrium_of(p, p->n_in, p->eps_in, p->beta_in, h, h + Q);
         else
-            orc_equilibrium(n[c], eps[c], b, p->c_l, h, h + Q);
+            equilibrium_of(p, n[c], eps[c], b, h, h + Q);
     }
     return 0;
 }
@@ -304,9 +418,20 @@ int orc_step(const orc_params* p, const uint8_t* solid, const double* in, double
                 double h[NPOP], m[5], feq[Q], geq[Q], beta[3], n, eps;
                 gather(p, solid, in, x, y, z, h);
                 orc_moments(h, p->c_l, m);
-                int bad = orc_recover(m, p->c_l, &n, &eps, beta);
-                int pos = positivity_flag(beta, p->c_l);
-                orc_equilibrium(n, eps, beta, p->c_l, feq, geq);
+                int bad, pos;
+                if (p->eos == EOS_GAMMA_LAW) {
+                    /* general EOS: the positivity counter flags any equilibrium <= 0 */
+                    double P;
+                    bad = orc_recover_general(m, p->c_l, p->eos_gamma, p->eos_mass, &n, &eps, &P, beta, NULL);
+                    orc_equilibrium_general(n, eps, P, beta, p->c_l, feq, geq);
+                    pos = 0;
+                    for (int i = 0; i < Q; ++i)
+                        if (!(feq[i] > 0.0) || !(geq[i] > 0.0)) pos = 1;
+                } else {
+                    bad = orc_recover(m, p->c_l, &n, &eps, beta);
+                    pos = positivity_flag(beta, p->c_l);
+                    orc_equilibrium(n, eps, beta, p->c_l, feq, geq);
+                }
                 double* o = out + c * NPOP;
                 for (int i = 0; i < Q; ++i) {
                     o[i] = h[i] - (h[i] - feq[i]) / p->tau;
@@ -340,7 +465,7 @@ int orc_step(const orc_params* p, const uint8_t* solid, const double* in, double
                 if (p->xbc == XBC_OUTFLOW_BOTH)
                     memcpy(out + g0 * NPOP, out + s0 * NPOP, sizeof(double) * NPOP);
                 else
-                    orc_equilibrium(p->n_in, p->eps_in, p->beta_in, p->c_l, out + g0 * NPOP, out + g0 * NPOP + Q);
+                    equilibrium_of(p, p->n_in, p->eps_in, p->beta_in, out + g0 * NPOP, out + g0 * NPOP + Q);
             }
     }
     if (st) {
@@ -381,9 +506,12 @@ int64_t orc_macro(const orc_params* p, const uint8_t* solid, const double* state
             n[c] = eps[c] = beta[c] = beta[N + c] = beta[2 * N + c] = NAN;
             continue;
         }
-        double m[5], b[3], nn, ep;
+        double m[5], b[3], nn, ep, P;
         orc_moments(state + c * NPOP, p->c_l, m);
-        bad += orc_recover(m, p->c_l, &nn, &ep, b);
+        if (p->eos == EOS_GAMMA_LAW)
+            bad += orc_recover_general(m, p->c_l, p->eos_gamma, p->eos_mass, &nn, &ep, &P, b, NULL);
+        else
+            bad += orc_recover(m, p->c_l, &nn, &ep, b);
         n[c] = nn;
         eps[c] = ep;
         beta[c] = b[0];
@@ -534,6 +662,7 @@ static double collision_adjoint(const double* h, const double* mu, double tau, d
  * step's contributions to *dtau and dbeta_in[3].                            */
 int orc_adjoint_step(const orc_params* p, const uint8_t* solid, const double* in_t, const double* lam_in,
                      double* lam_out, double* dtau, double* dbeta_in) {
+    if (p->eos != EOS_ULTRA) return -1; /* the adjoint covers eps = 3P */
     int nx = p->nx, ny = p->ny, nz = p->nz;
     int64_t N = (int64_t)nx * ny * nz;
     memset(lam_out, 0, sizeof(double) * NPOP * N);
@@ -597,6 +726,7 @@ int orc_adjoint_step(const orc_params* p, const uint8_t* solid, const double* in
  * sqrt(1 - |beta|^2).  Solid cells get zero.                               */
 int orc_adjoint_macro(const orc_params* p, const uint8_t* solid, const double* state, const double* dn,
                       const double* deps, const double* dbeta, double* lam) {
+    if (p->eos != EOS_ULTRA) return -1; /* the adjoint covers eps = 3P */
     int64_t N = (int64_t)p->nx * p->ny * p->nz;
     for (int64_t c = 0; c < N; ++c) {
         double* l = lam + c * NPOP;
@@ -636,6 +766,7 @@ int orc_adjoint_macro(const orc_params* p, const uint8_t* solid, const double* s
 int orc_adjoint_fields(const orc_params* p, const uint8_t* solid, const double* n, const double* eps,
                        const double* beta, const double* lam0, double* dn, double* deps, double* dbeta,
                        double* dbeta_in) {
+    if (p->eos != EOS_ULTRA) return -1; /* the adjoint covers eps = 3P */
     int64_t N = (int64_t)p->nx * p->ny * p->nz;
     double dIn[NPOP][5];
     if (p->xbc == XBC_INFLOW_OUTFLOW) deq_dfields(p->n_in, p->eps_in, p->beta_in, p->c_l, dIn);
