@@ -74,17 +74,27 @@ typedef enum { RLB_BC_PERIODIC = 0, RLB_BC_INFLOW_OUTFLOW = 1, RLB_BC_OUTFLOW_BO
 
 typedef enum { RLB_HOST = 0, RLB_DEVICE = 1 } rlb_where;
 
+/* Equation of state.  RLB_EOS_ULTRA: eps = 3P, the equilibria of Eqs.
+ * (equil1s), (equil2as), (equil2bs) with the closed-form recovery.
+ * RLB_EOS_GAMMA_LAW: an ideal gas with rest mass, P = (eos_gamma - 1)
+ * (eps - n eos_mass), the general equilibria of Eqs. (equil1), (equil2a),
+ * (equil2b) and the macroscopic constraints after Fig. 2, inverted by a
+ * Newton iteration on P; FP64 states only, no discrete adjoint.            */
+typedef enum { RLB_EOS_ULTRA = 0, RLB_EOS_GAMMA_LAW = 1 } rlb_eos;
+
 typedef struct {
     int32_t nx, ny, nz;   /* lattice size; nx >= 3 unless periodic; N < 2^31           */
     int32_t prec;         /* rlb_precision                                              */
     int32_t xbc;          /* rlb_xbc                                                    */
-    int32_t reserved;     /* must be 0                                                  */
+    int32_t eos;          /* rlb_eos                                                    */
     double tau;           /* BGK relaxation time in steps, tau > 1/2 (Eqs. lbe1, lbe2)  */
     double c_l;           /* lattice speed dx/dt in units of c (c_l > 1: "tachyons")    */
     double n_in, eps_in;  /* inflow state (RLB_BC_INFLOW_OUTFLOW)                       */
     double beta_in[3];
     double n_ref, eps_ref;/* RLB_FP32_DEV reference: populations are stored as
                              f - f^eq(n_ref, eps_ref, beta = 0); must be > 0           */
+    double eos_gamma;     /* RLB_EOS_GAMMA_LAW: adiabatic index, 1 < Gamma <= 2         */
+    double eos_mass;      /* RLB_EOS_GAMMA_LAW: particle rest mass m >= 0               */
 } rlb_params;
 
 /* Size of one state: plane stride in elements and element size in bytes;

@@ -19,6 +19,7 @@ RLB_OK, RLB_ERR_ARG, RLB_ERR_OOM, RLB_ERR_CUDA, RLB_ERR_UNPHYSICAL, RLB_ERR_STAT
 RLB_FP64, RLB_FP32_DEV = 0, 1
 RLB_BC_PERIODIC, RLB_BC_INFLOW_OUTFLOW, RLB_BC_OUTFLOW_BOTH = 0, 1, 2
 RLB_HOST, RLB_DEVICE = 0, 1
+RLB_EOS_ULTRA, RLB_EOS_GAMMA_LAW = 0, 1
 
 # Every symbol include/rlb.h declares.
 EXPORTS = (
@@ -37,10 +38,11 @@ class RLBError(RuntimeError):
 
 class rlb_params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
-                ("prec", ctypes.c_int32), ("xbc", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("prec", ctypes.c_int32), ("xbc", ctypes.c_int32), ("eos", ctypes.c_int32),
                 ("tau", ctypes.c_double), ("c_l", ctypes.c_double),
                 ("n_in", ctypes.c_double), ("eps_in", ctypes.c_double), ("beta_in", ctypes.c_double * 3),
-                ("n_ref", ctypes.c_double), ("eps_ref", ctypes.c_double)]
+                ("n_ref", ctypes.c_double), ("eps_ref", ctypes.c_double),
+                ("eos_gamma", ctypes.c_double), ("eos_mass", ctypes.c_double)]
 
 
 _lib = None
@@ -127,9 +129,11 @@ def _check(status: int, ctx=None, allow=()) -> int:
 
 
 def make_params(nx, ny, nz, tau, c_l=1.0, prec=RLB_FP64, xbc=RLB_BC_PERIODIC, n_in=1.0, eps_in=1.0,
-                beta_in=(0.0, 0.0, 0.0), n_ref=1.0, eps_ref=1.0) -> rlb_params:
+                beta_in=(0.0, 0.0, 0.0), n_ref=1.0, eps_ref=1.0, eos=RLB_EOS_ULTRA, eos_gamma=4.0 / 3.0,
+                eos_mass=0.0) -> rlb_params:
     p = rlb_params()
-    p.nx, p.ny, p.nz, p.prec, p.xbc, p.reserved = int(nx), int(ny), int(nz), int(prec), int(xbc), 0
+    p.nx, p.ny, p.nz, p.prec, p.xbc, p.eos = int(nx), int(ny), int(nz), int(prec), int(xbc), int(eos)
+    p.eos_gamma, p.eos_mass = float(eos_gamma), float(eos_mass)
     p.tau, p.c_l, p.n_in, p.eps_in = float(tau), float(c_l), float(n_in), float(eps_in)
     for a in range(3):
         p.beta_in[a] = float(beta_in[a])

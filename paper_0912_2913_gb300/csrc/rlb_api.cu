@@ -83,7 +83,12 @@ rlb_status check_params(const rlb_params* p) {
     if (p->prec != RLB_FP64 && p->prec != RLB_FP32_DEV) return fail(nullptr, RLB_ERR_ARG, "bad precision %d", p->prec);
     if (p->xbc < RLB_BC_PERIODIC || p->xbc > RLB_BC_OUTFLOW_BOTH) return fail(nullptr, RLB_ERR_ARG, "bad xbc %d", p->xbc);
     if (p->xbc != RLB_BC_PERIODIC && p->nx < 3) return fail(nullptr, RLB_ERR_ARG, "ghost planes need nx >= 3");
-    if (p->reserved != 0) return fail(nullptr, RLB_ERR_ARG, "reserved must be 0");
+    if (p->eos != RLB_EOS_ULTRA && p->eos != RLB_EOS_GAMMA_LAW) return fail(nullptr, RLB_ERR_ARG, "bad eos %d", p->eos);
+    if (p->eos == RLB_EOS_GAMMA_LAW) {
+        if (p->prec != RLB_FP64) return fail(nullptr, RLB_ERR_ARG, "the general equation of state runs in FP64");
+        if (!(p->eos_gamma > 1.0 && p->eos_gamma <= 2.0)) return fail(nullptr, RLB_ERR_ARG, "eos_gamma must be in (1, 2]");
+        if (!(p->eos_mass >= 0.0) || !isfinite(p->eos_mass)) return fail(nullptr, RLB_ERR_ARG, "eos_mass must be >= 0");
+    }
     if (!(p->tau > 0.5) || !isfinite(p->tau)) return fail(nullptr, RLB_ERR_ARG, "tau must be > 1/2");
     if (!(p->c_l > 0.0) || !isfinite(p->c_l)) return fail(nullptr, RLB_ERR_ARG, "c_l must be > 0");
     if (p->xbc == RLB_BC_INFLOW_OUTFLOW) {
@@ -216,6 +221,9 @@ rlb_status rlb_create(const rlb_params* p, void* stream, void* workspace, size_t
     for (int a = 0; a < 3; ++a) ph.beta_in[a] = p->beta_in[a];
     ph.n_ref = p->n_ref;
     ph.eps_ref = p->eps_ref;
+    ph.eos = p->eos;
+    ph.eos_gamma = p->eos == RLB_EOS_GAMMA_LAW ? p->eos_gamma : 4.0 / 3.0;
+    ph.eos_mass = p->eos == RLB_EOS_GAMMA_LAW ? p->eos_mass : 0.0;
     if (workspace) {
         c->ws = workspace;
         c->own_ws = false;
@@ -303,7 +311,10 @@ rlb_status rlb_init_fields(rlb_ctx* c, const double* n, const double* eps, const
         RLB_CUDA(c, cudaStreamSynchronize(c->stream), "sync");
         if (bad) return fail(c, RLB_ERR_ARG, "solid cells on a ghost plane or its neighbour (x = 0, 1, nx-2, nx-1)");
     }
-    rlb_status s = after_launch(c, launch_init(c->p.prec, g, c->ph, dn, de, db, ds, c->A, c->B, c->stream), "init");
+    rlb_status s = after_launch(c,
+                                c->ph.eos ? launch_init_eos(g, c->ph, dn, de, db, ds, c->A, c->B, c->stream)
+                                          : launch_init(c->p.prec, g, c->ph, dn, de, db, ds, c->A, c->B, c->stream),
+                                "init");
     if (s != RLB_OK) return s;
     if (tmp) {
         RLB_CUDA(c, cudaFreeAsync(tmp, c->stream), "cudaFreeAsync (init staging)");
@@ -369,7 +380,10 @@ rlb_status rlb_step(rlb_ctx* c, int32_t nsteps) {
         }
     }
     for (int32_t t = 0; t < nsteps; ++t) {
-        rlb_status s = after_launch(c, launch_step(c->p.prec, c->g, c->ph, c->A, c->B, c->cnt, true, c->steps, c->stream),
+        rlb_status s = after_launch(c,
+                                    c->ph.eos ? launch_step_eos(c->g, c->ph, c->A, c->B, c->cnt, true, c->steps, c->stream)
+                                              : launch_step(c->p.prec, c->g, c->ph, c->A, c->B, c->cnt, true, c->steps,
+                                                            c->stream),
                                     "step");
         if (s != RLB_OK) return s;
         void* tmp = c->A;
@@ -384,7 +398,10 @@ rlb_status rlb_step_into(rlb_ctx* c, const void* src, void* dst) {
     RLB_LATCHED(c);
     if (!src || !dst || src == dst) return fail(c, RLB_ERR_ARG, "src and dst must be distinct device buffers");
     if (c->g.variant < 0) c->g.variant = 1;
-    return after_launch(c, launch_step(c->p.prec, c->g, c->ph, src, dst, c->cnt, false, 0, c->stream), "step_into");
+    return after_launch(c,
+                        c->ph.eos ? launch_step_eos(c->g, c->ph, src, dst, c->cnt, false, 0, c->stream)
+                                  : launch_step(c->p.prec, c->g, c->ph, src, dst, c->cnt, false, 0, c->stream),
+                        "step_into");
 }
 
 rlb_status rlb_state_ptr(rlb_ctx* c, void** state) {
@@ -425,7 +442,10 @@ rlb_status rlb_macro(rlb_ctx* c, const void* state, double* n, double* eps, doub
         db = dn + 2 * N;
     }
     RLB_CUDA(c, cudaMemsetAsync(c->cnt.macro_bad, 0, sizeof(unsigned long long), c->stream), "memset");
-    rlb_status s = after_launch(c, launch_macro(c->p.prec, c->g, c->ph, A, dn, de, db, c->cnt, c->stream), "macro");
+    rlb_status s = after_launch(c,
+                                c->ph.eos ? launch_macro_eos(c->g, c->ph, A, dn, de, db, c->cnt, c->stream)
+                                          : launch_macro(c->p.prec, c->g, c->ph, A, dn, de, db, c->cnt, c->stream),
+                                "macro");
     if (s != RLB_OK) return s;
     if (tmp) {
         RLB_CUDA(c, cudaMemcpyAsync(n, dn, N * 8, cudaMemcpyDeviceToHost, c->stream), "copy n");
@@ -475,6 +495,7 @@ rlb_status rlb_stats(rlb_ctx* c, int64_t* steps, int64_t* n_unphysical, int64_t*
 rlb_status rlb_adjoint_macro(rlb_ctx* c, const void* state, const double* dL_dn, const double* dL_deps,
                              const double* dL_dbeta, void* lam_out) {
     RLB_LATCHED(c);
+    if (c->ph.eos) return fail(c, RLB_ERR_ARG, "the discrete adjoint covers the eps = 3P equation of state");
     if (!state || !dL_dn || !dL_deps || !dL_dbeta || !lam_out) return fail(c, RLB_ERR_ARG, "null pointer");
     return after_launch(c, launch_adjoint_macro(c->p.prec, c->g, c->ph, state, dL_dn, dL_deps, dL_dbeta, lam_out,
                                                 c->stream),
@@ -484,6 +505,7 @@ rlb_status rlb_adjoint_macro(rlb_ctx* c, const void* state, const double* dL_dn,
 rlb_status rlb_adjoint_step(rlb_ctx* c, const void* state_t, const void* lam_in, void* lam_out, double* dL_dtau_accum,
                             double* dL_dbeta_in_accum) {
     RLB_LATCHED(c);
+    if (c->ph.eos) return fail(c, RLB_ERR_ARG, "the discrete adjoint covers the eps = 3P equation of state");
     if (!state_t || !lam_in || !lam_out || lam_in == lam_out) return fail(c, RLB_ERR_ARG, "bad buffers");
     if (!dL_dtau_accum || !dL_dbeta_in_accum) return fail(c, RLB_ERR_ARG, "accumulators are required");
     return after_launch(c, launch_adjoint_step(c->p.prec, c->g, c->ph, state_t, lam_in, lam_out, c->red, c->inflow_d,
@@ -494,6 +516,7 @@ rlb_status rlb_adjoint_step(rlb_ctx* c, const void* state_t, const void* lam_in,
 rlb_status rlb_adjoint_step_noalloc(rlb_ctx* c, const void* state_t, const void* lam_in, void* lam_out,
                                     double* dL_dtau_accum, double* dL_dbeta_in_accum) {
     RLB_LATCHED(c);
+    if (c->ph.eos) return fail(c, RLB_ERR_ARG, "the discrete adjoint covers the eps = 3P equation of state");
     if (!state_t || !lam_in || !lam_out || lam_in == lam_out) return fail(c, RLB_ERR_ARG, "bad buffers");
     if (!dL_dtau_accum || !dL_dbeta_in_accum) return fail(c, RLB_ERR_ARG, "accumulators are required");
     int dev = -1;
@@ -515,6 +538,7 @@ rlb_status rlb_adjoint_step_noalloc(rlb_ctx* c, const void* state_t, const void*
 rlb_status rlb_adjoint_fields(rlb_ctx* c, const double* n0, const double* eps0, const double* beta0, const void* lam0,
                               double* dL_dn0, double* dL_deps0, double* dL_dbeta0, double* dL_dbeta_in_accum) {
     RLB_LATCHED(c);
+    if (c->ph.eos) return fail(c, RLB_ERR_ARG, "the discrete adjoint covers the eps = 3P equation of state");
     if (!n0 || !eps0 || !beta0 || !lam0 || !dL_dn0 || !dL_deps0 || !dL_dbeta0 || !dL_dbeta_in_accum)
         return fail(c, RLB_ERR_ARG, "null pointer");
     if (!c->inited) return fail(c, RLB_ERR_STATE, "rlb_adjoint_fields needs the solid layout of rlb_init_fields");

@@ -25,27 +25,6 @@ int g_last_launches = 0;
 int last_launch_count() { return g_last_launches; }
 void set_last_launch_count(int n) { g_last_launches = n; }
 
-// ---------------------------------------------------------------------------
-// Moments in pair form: S = sum f, E = sum g, M = c_l sum g e.
-// ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ void moments_pairs(const T* f, const T* g, T& sf, T& e, T& mx, T& my, T& mz) {
-    T s = f[0];
-#pragma unroll
-    for (int i = 1; i < 19; ++i) s += f[i];
-    T d[9];
-    T es = g[0];
-#pragma unroll
-    for (int p = 0; p < 9; ++p) {
-        es += g[2 * p + 1] + g[2 * p + 2];
-        d[p] = g[2 * p + 1] - g[2 * p + 2];
-    }
-    sf = s;
-    e = es;
-    mx = d[0] + d[3] + d[4] + d[5] + d[6];
-    my = d[1] + d[3] - d[4] + d[7] + d[8];
-    mz = d[2] + d[5] - d[6] + d[7] - d[8];
-}
 
 // ---------------------------------------------------------------------------
 // FP64 step.

@@ -48,6 +48,8 @@ struct Phys {
     double inv_cl, inv_cl2;
     double n_in, eps_in, beta_in[3];
     double n_ref, eps_ref;  // FP32 deviation reference (beta = 0)
+    int eos;                // 0: eps = 3P; 1: P = (eos_gamma - 1)(eps - n eos_mass)
+    double eos_gamma, eos_mass;
 };
 
 // Binary32 constants of the FP32 deviation step.
@@ -105,6 +107,14 @@ cudaError_t launch_adjoint_fields(int prec, const Geom& g, const Phys& ph, const
                                   const double* beta0, const void* A0, const void* lam0, double* dn0,
                                   double* deps0, double* dbeta0, double* red, double* dbeta_in,
                                   cudaStream_t stream);
+
+// General equation of state (FP64): initialisation, step and macro output.
+cudaError_t launch_init_eos(const Geom& g, const Phys& ph, const double* n, const double* eps, const double* beta,
+                            const uint8_t* solid, void* A, void* B, cudaStream_t stream);
+cudaError_t launch_step_eos(const Geom& g, const Phys& ph, const void* A, void* B, Counters cnt, bool count,
+                            long long step_index, cudaStream_t stream);
+cudaError_t launch_macro_eos(const Geom& g, const Phys& ph, const void* A, double* n, double* eps, double* beta,
+                             Counters cnt, cudaStream_t stream);
 
 // Kernel launches issued by the last launcher call (for accounting).
 int last_launch_count();

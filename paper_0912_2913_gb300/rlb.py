@@ -13,6 +13,7 @@ import torch
 from . import _native as N
 
 _PREC = {"fp64": N.RLB_FP64, "fp32": N.RLB_FP32_DEV, "fp32dev": N.RLB_FP32_DEV}
+_EOS = {"ultra": N.RLB_EOS_ULTRA, "gamma_law": N.RLB_EOS_GAMMA_LAW}
 _XBC = {"periodic": N.RLB_BC_PERIODIC, "inflow_outflow": N.RLB_BC_INFLOW_OUTFLOW,
         "outflow_both": N.RLB_BC_OUTFLOW_BOTH}
 
@@ -27,11 +28,14 @@ class RLB:
     """A D3Q19 relativistic lattice Boltzmann lattice (f and g populations) on one GPU."""
 
     def __init__(self, nx, ny, nz, tau, c_l=1.0, precision="fp64", xbc="periodic", n_in=1.0, eps_in=1.0,
-                 beta_in=(0.0, 0.0, 0.0), n_ref=1.0, eps_ref=1.0, device=None, stream=None):
+                 beta_in=(0.0, 0.0, 0.0), n_ref=1.0, eps_ref=1.0, device=None, stream=None, eos="ultra",
+                 eos_gamma=4.0 / 3.0, eos_mass=0.0):
         self.device = _require_cuda(device)
         prec = _PREC[precision] if isinstance(precision, str) else int(precision)
         x = _XBC[xbc] if isinstance(xbc, str) else int(xbc)
-        self.params = N.make_params(nx, ny, nz, tau, c_l, prec, x, n_in, eps_in, beta_in, n_ref, eps_ref)
+        e = _EOS[eos] if isinstance(eos, str) else int(eos)
+        self.params = N.make_params(nx, ny, nz, tau, c_l, prec, x, n_in, eps_in, beta_in, n_ref, eps_ref, e,
+                                    eos_gamma, eos_mass)
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.N = self.nx * self.ny * self.nz
         self.precision = "fp64" if prec == N.RLB_FP64 else "fp32"
@@ -65,8 +69,11 @@ class RLB:
         if eps_ref is None:
             eps_ref = cls.reference_value(np.append(w.eps[m], w.eps_in))
         xbc = {0: "periodic", 1: "inflow_outflow", 2: "outflow_both"}[w.xbc]
+        eos = dict(eos=getattr(w, "eos", 0), eos_gamma=getattr(w, "eos_gamma", 4.0 / 3.0),
+                   eos_mass=getattr(w, "eos_mass", 0.0))
+        eos.update(kw)
         return cls(w.nx, w.ny, w.nz, w.tau, w.c_l, precision, xbc, w.n_in, w.eps_in, w.beta_in, n_ref, eps_ref,
-                   device=device, **kw)
+                   device=device, **eos)
 
     # -- memory ---------------------------------------------------------------
     def new_state(self) -> torch.Tensor:

@@ -53,15 +53,20 @@ def test_parameter_validation(native):
         N.make_params(4, 4, 4, 0.8, xbc=N.RLB_BC_INFLOW_OUTFLOW, beta_in=(1.0, 0.0, 0.0)),
         N.make_params(4, 4, 4, 0.8, prec=N.RLB_FP32_DEV, n_ref=0.0),
         N.make_params(2048, 2048, 1024, 0.8),  # N >= 2^31
+        N.make_params(4, 4, 4, 0.8, prec=N.RLB_FP32_DEV, eos=N.RLB_EOS_GAMMA_LAW, eos_gamma=5 / 3),  # FP64 only
+        N.make_params(4, 4, 4, 0.8, eos=N.RLB_EOS_GAMMA_LAW, eos_gamma=1.0),  # 1 < Gamma <= 2
+        N.make_params(4, 4, 4, 0.8, eos=N.RLB_EOS_GAMMA_LAW, eos_gamma=2.5),
+        N.make_params(4, 4, 4, 0.8, eos=N.RLB_EOS_GAMMA_LAW, eos_gamma=1.5, eos_mass=-1.0),
     ]
     for p in bad:
         with pytest.raises(N.RLBError) as ei:
             N.rlb_state_layout(p)
         assert ei.value.status == N.RLB_ERR_ARG
     p = N.make_params(4, 4, 4, 0.8)
-    p.reserved = 1
+    p.eos = 2
     with pytest.raises(N.RLBError):
         N.rlb_workspace_bytes(p)
+    N.rlb_state_layout(N.make_params(4, 4, 4, 0.8, eos=N.RLB_EOS_GAMMA_LAW, eos_gamma=5 / 3, eos_mass=0.5))
     assert N.rlb_status_str(N.RLB_ERR_UNPHYSICAL) == "RLB_ERR_UNPHYSICAL"
 
 

@@ -60,14 +60,20 @@ class Workload:
     eps_in: float = 1.0
     beta_in: tuple = (0.0, 0.0, 0.0)
     extra: dict = field(default_factory=dict)
+    eos: int = 0  # 0: eps = 3P; 1: P = (eos_gamma - 1)(eps - n eos_mass)
+    eos_gamma: float = 4.0 / 3.0
+    eos_mass: float = 0.0
 
     @property
     def N(self) -> int:
         return self.nx * self.ny * self.nz
 
     def params(self) -> dict:
-        return dict(nx=self.nx, ny=self.ny, nz=self.nz, tau=self.tau, c_l=self.c_l, xbc=self.xbc,
-                    n_in=self.n_in, eps_in=self.eps_in, beta_in=tuple(self.beta_in))
+        d = dict(nx=self.nx, ny=self.ny, nz=self.nz, tau=self.tau, c_l=self.c_l, xbc=self.xbc,
+                 n_in=self.n_in, eps_in=self.eps_in, beta_in=tuple(self.beta_in))
+        if self.eos:
+            d.update(eos=self.eos, eos_gamma=self.eos_gamma, eos_mass=self.eos_mass)
+        return d
 
 
 def shock_tube_1d(nx: int = 1600, tau: float = 0.9, steps: int = 2000, eps_l: float = 1.0, n_l: float = 1.0,
