@@ -290,6 +290,25 @@ def oracle_thread_scaling(w, budget_s=2.0):
     return res
 
 
+def gamma_law_leg(w, steps, device, peak, ms_eps3p):
+    """The FP64 step with the general equation of state (an ideal gas with
+    rest mass, Gamma = 1.2, m = 0.3: Newton recovery) on the same workload."""
+    import torch
+
+    from paper_0912_2913_gb300 import RLB
+
+    sim = RLB.from_workload(w, "fp64", device=device, eos="gamma_law", eos_gamma=1.2, eos_mass=0.3)
+    sim.init_fields(w.n, w.eps, w.beta, w.solid)
+    ms, _ = time_forward(sim, steps, 3, 1, device)
+    st = sim.stats()
+    sim.close()
+    torch.cuda.empty_cache()
+    leg = _leg(w, ms, steps, BYTES_FWD["fp64"], peak,
+               {"eos": "P = (Gamma - 1)(eps - n m), Gamma = 1.2, m = 0.3", "bound": "alu",
+                "ratio_to_eps3p_step": (ms / steps) / ms_eps3p, "n_unphysical": st["n_unphysical"]})
+    return leg
+
+
 def shock_tube_graph_leg(device, steps_per_graph=100, replays=20):
     """The launch-bound 1D shock tube (1600 cells, FP64): microseconds per step
     with one rlb_step call per 1000 steps, and with steps_per_graph steps
@@ -440,6 +459,7 @@ def run_ours(args):
                 legs["fp64_adjoint"] = _leg(w, ms_all, ka, BYTES_ADJ["fp64"] + BYTES_FWD["fp64"], peak,
                                             {"adjoint_kernel_ms": ms_k / ka,
                                              "ratio_to_forward": (ms_all / ka) / (ms64 / k64)})
+            legs["fp64_gamma_law_forward"] = gamma_law_leg(w, k64, device, peak, ms64 / k64)
             legs["shock_tube_fp64"] = shock_tube_graph_leg(device)
         sim.close()
         del sim
