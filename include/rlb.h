@@ -10,7 +10,9 @@
  * (Eqs. lbe1, lbe2, equil1s, equil2as, equil2bs); the macroscopic fields n,
  * eps, beta come from the moment constraints n gamma = sum f_i,
  * (4/3) eps (gamma^2 - 1/4) = sum g_i, (4/3) eps gamma^2 u = sum g_i c_i
- * with eps = 3P.
+ * with eps = 3P.  Optionally (rlb_eos) the general equilibria of Eqs. equil1,
+ * equil2a, equil2b with (eps + P) gamma^2 - P = sum g_i,
+ * (eps + P) gamma^2 u = sum g_i c_i and an ideal-gas equation of state.
  *
  * Conventions common to every entry point:
  *  - Lattice: nx * ny * nz cells, x fastest; cell = (z*ny + y)*nx + x.  y and
@@ -128,7 +130,8 @@ RLB_API rlb_status rlb_init_fields(rlb_ctx* ctx, const double* n, const double* 
 /* Enqueue nsteps time steps of Eqs. (lbe1), (lbe2) on the context's state
  * (fused pull streaming with link bounce-back, moments, eps = 3P recovery,
  * equilibria Eqs. (equil1s, equil2as, equil2bs), BGK relaxation, boundary
- * planes).  Asynchronous, except that the first call on an RLB_FP32_DEV
+ * planes; under RLB_EOS_GAMMA_LAW the Newton recovery and Eqs. (equil1,
+ * equil2a, equil2b)).  Asynchronous, except that the first call on an RLB_FP32_DEV
  * context times its launch variants (bit-identical results) on the
  * context's second buffer and synchronises once; make that first call
  * before any stream capture.  nsteps >= 0.                                  */
@@ -148,7 +151,8 @@ RLB_API rlb_status rlb_save_state(rlb_ctx* ctx, void* dst);
 RLB_API rlb_status rlb_load_state(rlb_ctx* ctx, const void* src);
 
 /* Macroscopic fields of a state (the moment constraints solved with
- * eps = 3P): n, eps (N values each) and beta (3N); NaN at solid cells.
+ * eps = 3P, or by the Newton recovery under RLB_EOS_GAMMA_LAW): n, eps (N
+ * values each) and beta (3N); NaN at solid cells.
  * state = NULL means the context's current state.  where = RLB_DEVICE
  * (device outputs) or RLB_HOST (host outputs).  Synchronises; returns
  * RLB_ERR_UNPHYSICAL when a non-solid cell of the state fails the recovery
@@ -164,7 +168,11 @@ RLB_API rlb_status rlb_macro(rlb_ctx* ctx, const void* state, double* n, double*
 RLB_API rlb_status rlb_stats(rlb_ctx* ctx, int64_t* steps, int64_t* n_unphysical, int64_t* first_bad,
                      int64_t* n_nonpositive_eq);
 
-/* ---- discrete adjoint (transpose of the exact Jacobian of the step) ---- */
+/* ---- discrete adjoint (transpose of the exact Jacobian of the step) ----
+ * Not in the paper: the transpose of the Jacobian of one step of Eqs. (lbe1),
+ * (lbe2) with the eps = 3P equilibria and recovery, boundary planes and
+ * bounce-back included.  Every adjoint entry point returns RLB_ERR_ARG on a
+ * NULL or aliased buffer and on an RLB_EOS_GAMMA_LAW context.               */
 
 /* lambda_T = (d macro / d state)^T (dL/dn, dL/deps, dL/dbeta) at the device
  * state 'state': device inputs of N, N and 3N float64; lam_out a device

@@ -20,7 +20,8 @@
 // that is a ghost plane), or the identity at solid cells (never updated).
 // dL/dtau = sum mu_i (h_i - eq_i)/tau^2 and, at the inflow plane (held at
 // eq(n_in, eps_in, beta_in)), dL/dbeta_in = sum lambda_{t+1} d eq/d beta_in
-// are reduced per block and then over blocks in a fixed order.
+// are summed per warp (binary32 for the FP32 path, binary64 otherwise) and
+// then over the warp partials in a fixed order (k_finalize).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
