@@ -10,8 +10,13 @@
 //     beta = M / (E + P),   eps = E - |M|^2 / (E + P),   n = D sqrt(1 - beta^2);
 // P solves r(P) = (Gamma - 1)(eps(P) - m n(P)) - P = 0, with
 //     r'(P) = (Gamma - 1)(beta^2 - m n beta^2 / ((E + P)(1 - beta^2))) - 1,
-// iterated from the rest-frame value (Gamma - 1)(E - m D) (raised above
-// |M| - E) until |dP| <= 1e-14 (P + E), at most 100 iterations.
+// started from the massless solution (the positive root of
+// X^2 - Gamma E X + (Gamma - 1)|M|^2 = 0 for X = E + P, then
+// P = (Gamma - 1)(eps - m n) at its eps and n) and iterated until
+// |dP| <= 1e-14 (P + E), at most 100 iterations.  Reciprocals and inverse
+// square roots are binary32 seeds refined by two FP64 Newton-Raphson steps
+// (x -> x (2 - a x) and y -> y (3 - a y^2)/2), which are far cheaper than the
+// IEEE FP64 sequences on this GPU's FP64 pipe.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -20,6 +25,20 @@
 namespace rlb {
 
 namespace {
+
+__device__ __forceinline__ double rcp64(double a) {
+    double x = f2d(__frcp_rn(d2f_seed(a)));
+    x = fma(x, fma(-a, x, 1.0), x);
+    x = fma(x, fma(-a, x, 1.0), x);
+    return x;
+}
+
+__device__ __forceinline__ double rsqrt64(double a) {
+    double y = f2d(rsqrtf(d2f_seed(a)));
+    y = y * fma(-0.5 * a * y, y, 1.5);
+    y = y * fma(-0.5 * a * y, y, 1.5);
+    return y;
+}
 
 __device__ __forceinline__ double eos_pressure(const Phys& ph, double n, double eps) {
     return (ph.eos_gamma - 1.0) * (eps - n * ph.eos_mass);
@@ -30,13 +49,14 @@ __device__ __forceinline__ double eos_pressure(const Phys& ph, double n, double 
 __device__ __forceinline__ void equilibrium_general(double n, double eps, double P, double bx, double by, double bz,
                                                     const Phys& ph, double* f, double* g) {
     const double b2 = bx * bx + by * by + bz * bz;
-    const double gam2 = 1.0 / (1.0 - b2);
-    const double gam = sqrt(gam2);
+    const double gam = rsqrt64(1.0 - b2);
+    const double gam2 = gam * gam;
     const double h = (eps + P) * gam2;
-    const double rest = 3.0 * P / ((P + eps) * gam2) * ph.inv_cl2;
+    const double pr = P * rcp64(h);  // P / ((P + eps) gamma^2)
+    const double rest = 3.0 * pr * ph.inv_cl2;
     const double ng = n * gam;
     f[0] = kW0 * ng;
-    g[0] = kW0 * h * (3.0 - 3.0 * P * (2.0 + ph.c_l * ph.c_l) / ((P + eps) * gam2) * ph.inv_cl2 - 1.5 * b2 * ph.inv_cl2);
+    g[0] = kW0 * h * (3.0 - 3.0 * pr * (2.0 + ph.c_l * ph.c_l) * ph.inv_cl2 - 1.5 * b2 * ph.inv_cl2);
     const double q[9] = {bx, by, bz, bx + by, bx - by, bx + bz, bx - bz, by + bz, by - bz};
 #pragma unroll
     for (int p = 0; p < 9; ++p) {
@@ -58,31 +78,42 @@ __device__ __forceinline__ bool recover_general(double D, double E, double mx, d
     const double M2 = mx * mx + my * my + mz * mz;
     const double g1 = ph.eos_gamma - 1.0;
     const double mass = ph.eos_mass;
-    double p = g1 * (E - mass * D);
-    const double lo = sqrt(M2) - E;
-    if (!(p > lo)) p = lo + 1e-3 * (E > 0.0 ? E : 1.0);
+    double p;
+    {
+        // massless solution: X = E + P, X^2 - Gamma E X + (Gamma - 1) M^2 = 0
+        const double ge = ph.eos_gamma * E;
+        const double disc = fma(ge, ge, -4.0 * g1 * M2);
+        const double X = 0.5 * (ge + disc * rsqrt64(disc));
+        const double rX = rcp64(X);
+        const double b2 = M2 * rX * rX;
+        const double omb = 1.0 - b2;
+        p = g1 * ((E - M2 * rX) - mass * D * (omb * rsqrt64(omb)));
+        const double lo = sqrt(M2) - E;
+        if (!(p > lo)) p = lo + 1e-3 * (E > 0.0 ? E : 1.0);
+    }
     bool conv = false;
     for (int it = 0; it < 100; ++it) {
-        const double W = E + p;
-        const double b2 = M2 / (W * W);
-        const double nn = D * sqrt(1.0 - b2);
-        const double ep = E - M2 / W;
+        const double rW = rcp64(E + p);
+        const double b2 = M2 * rW * rW;
+        const double rs = rsqrt64(1.0 - b2);
+        const double nn = D * ((1.0 - b2) * rs);
+        const double ep = E - M2 * rW;
         const double r = g1 * (ep - mass * nn) - p;
-        const double dr = g1 * (b2 - mass * nn * b2 / (W * (1.0 - b2))) - 1.0;
-        const double dp = -r / dr;
+        const double dr = g1 * (b2 - mass * D * rs * b2 * rW) - 1.0;  // n / (1 - b2) = D rs
+        const double dp = -r * rcp64(dr);
         p = p + dp;
         if (fabs(dp) <= 1e-14 * (fabs(p) + fabs(E))) {
             conv = true;
             break;
         }
     }
-    const double W = E + p;
-    bx = mx / W;
-    by = my / W;
-    bz = mz / W;
+    const double rW = rcp64(E + p);
+    bx = mx * rW;
+    by = my * rW;
+    bz = mz * rW;
     const double b2 = bx * bx + by * by + bz * bz;
-    n = D * sqrt(1.0 - b2);
-    eps = E - M2 / W;
+    n = D * ((1.0 - b2) * rsqrt64(1.0 - b2));
+    eps = E - M2 * rW;
     P = p;
     return !(conv && pos_finite(D) && pos_finite(E) && pos_finite(p) && below_one(b2) && isfinite(n) &&
              isfinite(eps) && isfinite(bx) && isfinite(by) && isfinite(bz));
