@@ -279,6 +279,39 @@ def test_oracle_taped_gradient_shock_tube_short():
     assert np.max(np.abs(de - de0)) <= 1e-9 * np.max(np.abs(de0))
 
 
+@pytest.mark.slow
+def test_random_box_512_fp32_adjoint_step_against_fp64():
+    """One adjoint step on the 512^3 box (38 S > 2^31: the staged FP32 kernel
+    runs with 64-bit element offsets): the FP32 adjoint against the FP64
+    adjoint of the same run after 20 steps, with the same random lambda_{t+1},
+    on the 64^3 lattice of cells x, y, z = 0 (mod 8) and in dL/dtau."""
+    from paper_0912_2913_gb300 import RLB
+
+    w = W.random_box(L=512, steps=20)
+    out = {}
+    for prec in ("fp64", "fp32"):
+        sim = RLB.from_workload(w, prec, device="cuda:0").init_fields(w.n, w.eps, w.beta)
+        if prec == "fp32":
+            assert 38 * sim.plane_stride >= 2 ** 31
+        sim.step(20)
+        g = torch.Generator(device="cuda").manual_seed(5)
+        lam = torch.randn((38, sim.plane_stride), generator=g, dtype=torch.float64, device="cuda")
+        li = lam.to(sim.dtype)
+        del lam
+        lo = torch.empty_like(li)
+        acc = torch.zeros(4, dtype=torch.float64, device="cuda")
+        sim.adjoint_step(sim.state(), li, lo, acc[0:1], acc[1:4])
+        sub = lo[:, :sim.N].view(38, 512, 512, 512)[:, ::8, ::8, ::8].double().cpu().numpy()
+        out[prec] = (sub, float(acc[0]))
+        sim.close()
+        del sim, li, lo
+        torch.cuda.empty_cache()
+    a, b = out["fp32"][0], out["fp64"][0]
+    assert np.isfinite(a).all()
+    assert np.max(np.abs(a - b)) / np.max(np.abs(b)) <= 1e-4
+    assert abs(out["fp32"][1] - out["fp64"][1]) <= 1e-3 * abs(out["fp64"][1])
+
+
 def _sphere_gradient_check(nx, ny, nz, T, plane):
     """Loss on the pressure P = eps/3 of the plane x = plane after T steps
     against a run with inflow beta_x = 0.45 (sqrt(T) checkpointing);
