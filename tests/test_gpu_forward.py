@@ -312,6 +312,20 @@ def test_errors_are_status_codes():
         sim.init_fields(*(torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (w.n, w.eps, w.beta)), dev_bad)
     sim.init_fields(w.n, w.eps, w.beta, w.solid).step(2)
     assert sim.stats()["steps"] == 2
+    before = sim.state().clone()
+    sim.step(0)  # an empty step request is a no-op
+    assert sim.stats()["steps"] == 2 and torch.equal(before.view(torch.int64), sim.state().view(torch.int64))
+    with pytest.raises(RLBError) as ei:
+        N.rlb_step(sim.ctx, -1)
+    assert ei.value.status == N.RLB_ERR_ARG
+    st = sim.new_state()
+    with pytest.raises(RLBError) as ei:
+        N.rlb_step_into(sim.ctx, st, st)  # src and dst must differ
+    assert ei.value.status == N.RLB_ERR_ARG
+    with pytest.raises(RLBError) as ei:
+        N.rlb_step(None, 1)
+    assert ei.value.status == N.RLB_ERR_ARG
+    assert sim.stats()["steps"] == 2  # the refused calls changed nothing
     sim.close()
 
 
