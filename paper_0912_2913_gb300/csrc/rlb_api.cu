@@ -2,6 +2,7 @@
 // workspace layout, host<->device marshalling and kernel launches on the
 // context's stream.  No arithmetic of the scheme lives here; every step of
 // the method runs in the kernels of rlb_forward.cu and rlb_adjoint.cu.
+#include <nvtx3/nvToolsExt.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
@@ -40,6 +41,20 @@ struct rlb_ctx {
 };
 
 namespace {
+
+// NVTX range around an entry point (visible in profilers; no cost without one).
+struct Nvtx {
+    explicit Nvtx(const char* name) { nvtxRangePushA(name); }
+    ~Nvtx() { nvtxRangePop(); }
+};
+
+// Allocation-failure injection for tests of the error path (host side only):
+// with RLB_INJECT_ALLOC_FAILURE=1 in the environment, rlb_create reports
+// RLB_ERR_OOM instead of allocating its workspace.
+bool inject_alloc_failure() {
+    const char* v = getenv("RLB_INJECT_ALLOC_FAILURE");
+    return v && v[0] == '1';
+}
 
 thread_local char g_msg[320] = "";
 
@@ -171,6 +186,8 @@ rlb_status rlb_create(const rlb_params* p, void* stream, void* workspace, size_t
         return fail(nullptr, RLB_ERR_ARG, "workspace too small: %zu < %zu bytes", workspace_bytes, need);
     if (workspace && ((uintptr_t)workspace % kAlign) != 0)
         return fail(nullptr, RLB_ERR_ARG, "workspace must be %zu-byte aligned", kAlign);
+    if (!workspace && inject_alloc_failure())
+        return fail(nullptr, RLB_ERR_OOM, "injected allocation failure (RLB_INJECT_ALLOC_FAILURE)");
     rlb_ctx* c = new (std::nothrow) rlb_ctx();
     if (!c) return fail(nullptr, RLB_ERR_OOM, "host allocation of the context failed");
     c->p = *p;
@@ -272,6 +289,7 @@ rlb_status rlb_destroy(rlb_ctx* c) {
 
 rlb_status rlb_init_fields(rlb_ctx* c, const double* n, const double* eps, const double* beta, const uint8_t* solid,
                            rlb_where where) {
+    Nvtx nvtx_("rlb_init_fields");
     RLB_LATCHED(c);
     if (!n || !eps || !beta) return fail(c, RLB_ERR_ARG, "n, eps and beta are required");
     if (where != RLB_HOST && where != RLB_DEVICE) return fail(c, RLB_ERR_ARG, "bad 'where'");
@@ -368,6 +386,7 @@ static rlb_status autotune_f32(rlb_ctx* c) {
 }
 
 rlb_status rlb_step(rlb_ctx* c, int32_t nsteps) {
+    Nvtx nvtx_("rlb_step");
     RLB_LATCHED(c);
     if (nsteps < 0) return fail(c, RLB_ERR_ARG, "nsteps must be >= 0");
     if (!c->inited) return fail(c, RLB_ERR_STATE, "rlb_step before rlb_init_fields");
@@ -395,6 +414,7 @@ rlb_status rlb_step(rlb_ctx* c, int32_t nsteps) {
 }
 
 rlb_status rlb_step_into(rlb_ctx* c, const void* src, void* dst) {
+    Nvtx nvtx_("rlb_step_into");
     RLB_LATCHED(c);
     if (!src || !dst || src == dst) return fail(c, RLB_ERR_ARG, "src and dst must be distinct device buffers");
     if (c->g.variant < 0) c->g.variant = 1;
@@ -427,6 +447,7 @@ rlb_status rlb_load_state(rlb_ctx* c, const void* src) {
 }
 
 rlb_status rlb_macro(rlb_ctx* c, const void* state, double* n, double* eps, double* beta, rlb_where where) {
+    Nvtx nvtx_("rlb_macro");
     RLB_LATCHED(c);
     if (!n || !eps || !beta) return fail(c, RLB_ERR_ARG, "outputs are required");
     if (where != RLB_HOST && where != RLB_DEVICE) return fail(c, RLB_ERR_ARG, "bad 'where'");
@@ -504,6 +525,7 @@ rlb_status rlb_adjoint_macro(rlb_ctx* c, const void* state, const double* dL_dn,
 
 rlb_status rlb_adjoint_step(rlb_ctx* c, const void* state_t, const void* lam_in, void* lam_out, double* dL_dtau_accum,
                             double* dL_dbeta_in_accum) {
+    Nvtx nvtx_("rlb_adjoint_step");
     RLB_LATCHED(c);
     if (c->ph.eos) return fail(c, RLB_ERR_ARG, "the discrete adjoint covers the eps = 3P equation of state");
     if (!state_t || !lam_in || !lam_out || lam_in == lam_out) return fail(c, RLB_ERR_ARG, "bad buffers");

@@ -121,6 +121,56 @@ class RLB:
     def load_state(self, src: torch.Tensor):
         N.rlb_load_state(self.ctx, src)
 
+    # -- checkpoint / resume through a host file ------------------------------
+    CHECKPOINT_FORMAT = "rlb-state-v1"
+
+    def _param_dict(self) -> dict:
+        out = {}
+        for name, _ in self.params._fields_:
+            v = getattr(self.params, name)
+            out[name] = list(v) if name == "beta_in" else v
+        return out
+
+    def save(self, path: str):
+        """Write the current state to a file: one JSON header line (every
+        rlb_params field, the layout, the steps taken) followed by the 38
+        planes as raw little-endian values of the state's element type.
+        ``load`` on a context with the same parameters resumes from it."""
+        import json
+
+        self.sync()
+        hdr = {"format": self.CHECKPOINT_FORMAT, "params": self._param_dict(), "plane_stride": self.plane_stride,
+               "elem_bytes": self.elem_bytes, "steps": self.stats()["steps"]}
+        data = self.state().detach().cpu().numpy()
+        with open(path, "wb") as fh:
+            fh.write((json.dumps(hdr) + "\n").encode())
+            fh.write(data.astype(data.dtype.newbyteorder("<"), copy=False).tobytes())
+        return self
+
+    def load(self, path: str):
+        """Resume from a file written by ``save``: the parameters and the layout
+        must match this context's (ValueError otherwise)."""
+        import json
+
+        with open(path, "rb") as fh:
+            hdr = json.loads(fh.readline().decode())
+            raw = fh.read()
+        if hdr.get("format") != self.CHECKPOINT_FORMAT:
+            raise ValueError(f"not an RLB state file: {path}")
+        if hdr["params"] != self._param_dict():
+            raise ValueError("the state file was written with other parameters")
+        if hdr["plane_stride"] != self.plane_stride or hdr["elem_bytes"] != self.elem_bytes:
+            raise ValueError("the state file has another layout")
+        dt = np.dtype("<f8" if self.elem_bytes == 8 else "<f4")
+        arr = np.frombuffer(raw, dtype=dt)
+        if arr.size != 38 * self.plane_stride:
+            raise ValueError("truncated state file")
+        t = torch.from_numpy(arr.reshape(38, self.plane_stride).astype(dt.newbyteorder("="))).to(self.device)
+        torch.cuda.synchronize(self.device)  # the copy above ran on torch's stream
+        N.rlb_load_state(self.ctx, t)
+        self.sync()
+        return self
+
     def macro(self, state: torch.Tensor | None = None, where: str = "device"):
         """(n, eps, beta, ok): n, eps (nz, ny, nx), beta (3, nz, ny, nx); NaN at solid cells;
         ok is False when some cell failed the recovery (outputs are still written)."""

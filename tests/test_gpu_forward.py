@@ -262,6 +262,29 @@ def test_cuda_graph_of_steps_matches_stream_steps(prec):
     sim.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_checkpoint_file_resume(prec, tmp_path):
+    """save() after 20 steps, load() into a fresh context and 15 more steps
+    give the state of 35 uninterrupted steps, bit for bit; a file written with
+    other parameters is refused."""
+    from paper_0912_2913_gb300 import RLB
+
+    w = W.sphere_3d(nx=40, ny=20, nz=18)
+    a = RLB.from_workload(w, prec, device="cuda:0").init_fields(w.n, w.eps, w.beta, w.solid).step(20)
+    path = str(tmp_path / "state.rlb")
+    a.save(path)
+    a.step(15)
+    b = RLB.from_workload(w, prec, device="cuda:0").load(path).step(15)
+    iv = torch.int64 if prec == "fp64" else torch.int32
+    assert torch.equal(a.state()[:, :a.N].view(iv), b.state()[:, :b.N].view(iv))
+    w2 = W.sphere_3d(nx=40, ny=20, nz=18, tau=0.9)
+    c = RLB.from_workload(w2, prec, device="cuda:0")
+    with pytest.raises(ValueError):
+        c.load(path)
+    for s in (a, b, c):
+        s.close()
+
+
 def test_step_into_matches_step():
     w = tiny_workload(12, 6, 5, 1, seed=5, solid_cells=((5, 3, 2),))
     from paper_0912_2913_gb300 import RLB

@@ -80,3 +80,14 @@ def test_product_does_not_import_the_oracle():
                     src = fh.read()
                 assert not re.search(r"^\s*(import|from)\s+oracle\b", src, re.M), f
                 assert "rlb_oracle" not in src, f
+
+
+def test_allocation_failure_is_reported(native, monkeypatch):
+    """A failing workspace allocation (injected on the host, before any CUDA
+    call) comes back as RLB_ERR_OOM with its message; nothing is created."""
+    N = native
+    monkeypatch.setenv("RLB_INJECT_ALLOC_FAILURE", "1")
+    with pytest.raises(N.RLBError) as ei:
+        N.rlb_create(N.make_params(16, 8, 4, 0.8), None, None, 0)
+    assert ei.value.status == N.RLB_ERR_OOM
+    assert "injected allocation failure" in N.rlb_last_error(None)
