@@ -316,6 +316,35 @@ def oracle_thread_scaling(w, budget_s=2.0):
     return res
 
 
+def accuracy_leg(w, steps, device):
+    """Max relative error of the FP32 deviation path against the FP64 path on
+    the benchmark workload after `steps` steps (n and eps relative per cell,
+    beta over max(max|beta|, 1e-3); solid cells excluded).  The FP64 GPU path
+    is held to the FP64 oracle within 1e-10 by the parity tests."""
+    import torch
+
+    from paper_0912_2913_gb300 import RLB
+
+    out = {}
+    for prec in ("fp64", "fp32"):
+        sim = RLB.from_workload(w, prec, device=device).init_fields(w.n, w.eps, w.beta, w.solid)
+        sim.step(steps)
+        n, e, b, _ = sim.macro()
+        out[prec] = (n, e, b, sim.stats()["n_unphysical"])
+        sim.close()
+    n0, e0, b0, u0 = out["fp64"]
+    n1, e1, b1, u1 = out["fp32"]
+    m = torch.isfinite(n0)
+    en = float(((n1 - n0).abs() / n0.abs())[m].max())
+    ee = float(((e1 - e0).abs() / e0.abs())[m].max())
+    bs = max(float(b0[:, m].abs().max()), 1e-3)
+    eb = float((b1 - b0)[:, m].abs().max()) / bs
+    del out
+    torch.cuda.empty_cache()
+    return {"reference": "FP64 GPU path (held to the FP64 oracle at 1e-10 by the parity tests)", "steps": steps,
+            "fp32_max_rel_err": {"n": en, "eps": ee, "beta": eb}, "unphysical": {"fp64": u0, "fp32": u1}}
+
+
 def gamma_law_leg(w, steps, device, peak, ms_eps3p):
     """The FP64 step with the general equation of state (an ideal gas with
     rest mass, Gamma = 1.2, m = 0.3: Newton recovery) on the same workload."""
@@ -491,6 +520,7 @@ def run_ours(args):
         del sim
         torch.cuda.empty_cache()
     clocks = clk.summary()
+    accuracy = accuracy_leg(w, min(args.steps, 1000), device) if (rank == 0 and not args.headline_only) else None
     e2e = None
     if rank == 0 and not args.no_e2e:
         e2e = e2e_run(w, args.e2e_steps, 1, device)
@@ -514,6 +544,7 @@ def run_ours(args):
             "legs": legs,
             "clocks": clocks,
             "e2e": e2e,
+            "accuracy": accuracy,
             "cpu_baseline": cpu,
             "gpu_launches": launches,
             "stats_fp32": stats32,
