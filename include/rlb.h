@@ -225,6 +225,20 @@ RLB_API rlb_status rlb_adjoint_fields(rlb_ctx* ctx, const double* n0, const doub
 RLB_API rlb_status rlb_selftest_conversions(const float* f_in, const double* d_in, int64_t n, double* f2d_out,
                                             float* d2f_out);
 
+/* Debug: out-of-range state-buffer indices the step, adjoint and general-EOS
+ * kernels met since the last call (the bounds-checking build, compiled with
+ * RLB_CHECK_BOUNDS, counts them and keeps every access inside its buffer;
+ * not in the paper).  Synchronises the current device.  The release build
+ * sets *count = -1 and returns RLB_ERR_STATE.                              */
+RLB_API rlb_status rlb_debug_bounds_violations(int64_t* count);
+
+/* Debug: runs the bounds build's index check on one index in a kernel on the
+ * legacy default stream (no memory is accessed with the index) and stores the
+ * checked index in *checked: `index` itself when 0 <= index < n, else 0, and
+ * the violation is counted as by the kernels.  The release build sets
+ * *checked = -1 and returns RLB_ERR_STATE.                                   */
+RLB_API rlb_status rlb_debug_bounds_selftest(int64_t index, int64_t n, int64_t* checked);
+
 /* Wait for the context's stream; returns a latched or new CUDA error.       */
 RLB_API rlb_status rlb_sync(rlb_ctx* ctx);
 

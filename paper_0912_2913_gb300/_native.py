@@ -26,7 +26,8 @@ EXPORTS = (
     "rlb_state_layout", "rlb_workspace_bytes", "rlb_create", "rlb_destroy", "rlb_init_fields", "rlb_step",
     "rlb_step_into", "rlb_state_ptr", "rlb_save_state", "rlb_load_state", "rlb_macro", "rlb_stats",
     "rlb_adjoint_macro", "rlb_adjoint_step", "rlb_adjoint_fields", "rlb_sync", "rlb_status_str", "rlb_last_error",
-    "rlb_launch_count", "rlb_selftest_conversions", "rlb_adjoint_step_noalloc",
+    "rlb_launch_count", "rlb_selftest_conversions", "rlb_adjoint_step_noalloc", "rlb_debug_bounds_violations",
+    "rlb_debug_bounds_selftest",
 )
 
 
@@ -49,25 +50,34 @@ _lib = None
 _lock = threading.Lock()
 
 
+def _bounds_variant() -> bool:
+    """RLB_LIBRARY_VARIANT=bounds loads the bounds-checking debug library."""
+    v = os.environ.get("RLB_LIBRARY_VARIANT", "release")
+    if v not in ("release", "bounds"):
+        raise ValueError(f"RLB_LIBRARY_VARIANT must be 'release' or 'bounds', not {v!r}")
+    return v == "bounds"
+
+
 def library_path() -> str:
     from . import build as _build
 
-    return _build.library_path()
+    return _build.library_path(bounds=_bounds_variant())
 
 
 def load(build_if_missing: bool = True):
-    """Load librlb.so (building it first if needed)."""
+    """Load librlb (building it first if needed)."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
         from . import build as _build
 
-        path = _build.library_path()
+        bounds = _bounds_variant()
+        path = _build.library_path(bounds=bounds)
         if not os.path.exists(path):
             if not build_if_missing:
                 raise RuntimeError(f"librlb is not built ({path}); run __graft_entry__.build()")
-            path = _build.build()
+            path = _build.build(bounds=bounds)
         L = ctypes.CDLL(path)
         vp, sz, i32, i64, dp = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
         P = ctypes.POINTER
@@ -94,6 +104,8 @@ def load(build_if_missing: bool = True):
             "rlb_last_error": ([vp], ctypes.c_char_p),
             "rlb_launch_count": ([vp], i64),
             "rlb_selftest_conversions": ([vp, vp, i64, vp, vp], st),
+            "rlb_debug_bounds_violations": ([P(i64)], st),
+            "rlb_debug_bounds_selftest": ([i64, i64, P(i64)], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -234,6 +246,20 @@ def rlb_last_error(ctx=None) -> str:
 
 def rlb_selftest_conversions(f_in, d_in, n, f2d_out, d2f_out) -> None:
     _check(load().rlb_selftest_conversions(_ptr(f_in), _ptr(d_in), int(n), _ptr(f2d_out), _ptr(d2f_out)))
+
+
+def rlb_debug_bounds_violations() -> int:
+    """Out-of-range state indices counted by the bounds-checking build."""
+    v = ctypes.c_int64()
+    _check(load().rlb_debug_bounds_violations(ctypes.byref(v)))
+    return v.value
+
+
+def rlb_debug_bounds_selftest(index: int, n: int) -> int:
+    """The bounds build's index check run on one index in a kernel."""
+    v = ctypes.c_int64()
+    _check(load().rlb_debug_bounds_selftest(index, n, ctypes.byref(v)))
+    return v.value
 
 
 def rlb_launch_count(ctx) -> int:

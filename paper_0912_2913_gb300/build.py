@@ -1,8 +1,13 @@
 """Build librlb.so in-tree with nvcc for sm_103a (GB300).
 
 Each .cu file compiles in its own nvcc process (in parallel); the objects are
-linked into ``paper_0912_2913_gb300/_build/librlb.so``.  A rebuild happens
-only when a source file changed (content hash in the library's file name).
+linked into ``paper_0912_2913_gb300/_build/librlb_<hash>.so``.  A rebuild
+happens only when a source file changed (content hash in the library's file
+name).  ``build(bounds=True)`` makes the bounds-checking debug library
+``librlb_bounds_<hash>.so`` (``-DRLB_CHECK_BOUNDS``: every state-buffer index
+of the step, adjoint and general-EOS kernels is range-checked and counted,
+``rlb_debug_bounds_violations`` reads the count); the release library is
+unaffected by it.
 """
 from __future__ import annotations
 
@@ -61,13 +66,18 @@ def unit_digest(source: str) -> str:
     return h.hexdigest()[:12]
 
 
-def library_path() -> str:
-    return os.path.join(BUILD, f"librlb_{_digest()}.so")
+def _prefix(bounds: bool) -> str:
+    return "librlb_bounds_" if bounds else "librlb_"
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    """Compile (if needed) and return the path of librlb.so."""
-    so = library_path()
+def library_path(bounds: bool = False) -> str:
+    return os.path.join(BUILD, f"{_prefix(bounds)}{_digest()}.so")
+
+
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, bounds: bool = False) -> str:
+    """Compile (if needed) and return the path of librlb_<hash>.so (of the
+    bounds-checking librlb_bounds_<hash>.so with ``bounds=True``)."""
+    so = library_path(bounds)
     if os.path.exists(so) and not force and not ptxas_info:
         return so
     os.makedirs(BUILD, exist_ok=True)
@@ -76,8 +86,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     extra = ["-Xptxas", "-v"] if ptxas_info else []
 
     def compile_one(src):
-        obj = os.path.join(BUILD, f"{os.path.splitext(src)[0]}_{tag}.o")
-        flags = list(NVCC_FLAGS)
+        obj = os.path.join(BUILD, f"{os.path.splitext(src)[0]}_{'b' if bounds else ''}{tag}.o")
+        flags = list(NVCC_FLAGS) + (["-DRLB_CHECK_BOUNDS"] if bounds else [])
         if src in FMAD_SOURCES:
             flags[flags.index("-fmad=false")] = "-fmad=true"
         cmd = [nvcc, *ARCH, *flags, *extra, "-I", INCLUDE, "-c", os.path.join(CSRC, src), "-o", obj]
@@ -99,9 +109,10 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     os.replace(tmp, so)
     for o, _ in results:
         os.remove(o)
-    # drop libraries of superseded sources
+    # drop libraries of superseded sources (of the same kind)
     for f in os.listdir(BUILD):
-        if f.startswith("librlb_") and f.endswith(".so") and os.path.join(BUILD, f) != so:
+        if (f.startswith(_prefix(bounds)) and f.endswith(".so") and f[len(_prefix(bounds)):-3].isalnum()
+                and os.path.join(BUILD, f) != so):
             try:
                 os.remove(os.path.join(BUILD, f))
             except OSError:
@@ -110,4 +121,5 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv,
+                bounds="--bounds" in sys.argv))

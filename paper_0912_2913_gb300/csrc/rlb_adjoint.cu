@@ -463,15 +463,15 @@ __device__ __forceinline__ void ghost_cell(int x, int idx, long long S, const T*
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
         if (vel_x(i) != inward) {
-            Lout[i * S + idx] = (T)0;
-            Lout[(19 + i) * S + idx] = (T)0;
+            Lout[RLB_CHK(i * S + idx, 38ll * S)] = (T)0;
+            Lout[RLB_CHK((19 + i) * S + idx, 38ll * S)] = (T)0;
         }
     }
-    if (XBC == XBC_INFLOW_OUTFLOW && x == 0 && !is_solid(A[idx])) {
+    if (XBC == XBC_INFLOW_OUTFLOW && x == 0 && !is_solid(A[RLB_CHK(idx, 38ll * S)])) {
         T a0 = 0, a1 = 0, a2 = 0;
 #pragma unroll 2
         for (int q = 0; q < 38; ++q) {
-            const T l = Lin[q * S + idx];
+            const T l = Lin[RLB_CHK(q * S + idx, 38ll * S)];
             a0 += l * (T)inflow_d[3 * q + 0];
             a1 += l * (T)inflow_d[3 * q + 1];
             a2 += l * (T)inflow_d[3 * q + 2];
@@ -491,8 +491,8 @@ __device__ __forceinline__ void zero_to_ghost(int x, int nx, int idx, long long 
         for (int i = 1; i < 19; ++i) {
             const bool to_ghost = (x == 1 && vel_x(i) == -1) || (x == nx - 2 && vel_x(i) == 1);
             if (to_ghost) {
-                Lout[i * S + idx] = (T)0;
-                Lout[(19 + i) * S + idx] = (T)0;
+                Lout[RLB_CHK(i * S + idx, 38ll * S)] = (T)0;
+                Lout[RLB_CHK((19 + i) * S + idx, 38ll * S)] = (T)0;
             }
         }
     }
@@ -524,9 +524,9 @@ __global__ void __launch_bounds__(128, MINB)
             ghost_cell<T, XBC>(x, idx, S, A, Lin, Lout, inflow_d, bin0, bin1, bin2, has_b);
             continue;
         }
-        if (is_solid(A[19 * S + idx])) {  // never updated: identity
+        if (is_solid(A[RLB_CHK(19 * S + idx, 38ll * S)])) {  // never updated: identity
 #pragma unroll
-            for (int q = 0; q < 38; ++q) Lout[q * S + idx] = Lin[q * S + idx];
+            for (int q = 0; q < 38; ++q) Lout[RLB_CHK(q * S + idx, 38ll * S)] = Lin[RLB_CHK(q * S + idx, 38ll * S)];
             continue;
         }
         const PullOffsets o(g, x, y, z);
@@ -536,25 +536,25 @@ __global__ void __launch_bounds__(128, MINB)
         // take branches, so the common cell runs straight-line loads/stores
         auto load_mu = [&](T* mu, int base) {
 #pragma unroll
-            for (int i = 0; i < 19; ++i) mu[i] = Lin[(base + i) * S + idx];
+            for (int i = 0; i < 19; ++i) mu[i] = Lin[RLB_CHK((base + i) * S + idx, 38ll * S)];
             if (dup) {
 #pragma unroll
-                for (int i = 0; i < 19; ++i) mu[i] += Lin[(base + i) * S + idx + dup];
+                for (int i = 0; i < 19; ++i) mu[i] += Lin[RLB_CHK((base + i) * S + idx + dup, 38ll * S)];
             }
         };
         if (!PIPE) {
             // f-phase populations and adjoints: start their trip from HBM into L2 now
 #pragma unroll
             for (int i = 0; i < 19; ++i) {
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(A + i * S + idx + o.src(i)));
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(Lin + i * S + idx));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(RLB_CHK_PTR(A, i * S + idx + o.src(i), 38ll * S)));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(RLB_CHK_PTR(Lin, i * S + idx, 38ll * S)));
             }
         }
         // ---- g phase: gather, moments, recovery, g part of the adjoint
         unsigned bounced = 0u;
         T h[19];
 #pragma unroll
-        for (int i = 0; i < 19; ++i) h[i] = A[(19 + i) * S + idx + o.src(i)];
+        for (int i = 0; i < 19; ++i) h[i] = A[RLB_CHK((19 + i) * S + idx + o.src(i), 38ll * S)];
         {
             // a pulled solid marker is a NaN: test the per-value markers only
             // when the sum of the gathered values is NaN
@@ -563,7 +563,7 @@ __global__ void __launch_bounds__(128, MINB)
                 for (int i = 1; i < 19; ++i) {
                     if (is_solid(h[i])) {
                         bounced |= 1u << i;
-                        h[i] = A[(19 + opp(i)) * S + idx];
+                        h[i] = A[RLB_CHK((19 + opp(i)) * S + idx, 38ll * S)];
                     }
                 }
             }
@@ -574,11 +574,11 @@ __global__ void __launch_bounds__(128, MINB)
         cell_g(h, mug, c, r);
         // ---- f phase
 #pragma unroll
-        for (int i = 0; i < 19; ++i) h[i] = A[i * S + idx + o.src(i)];
+        for (int i = 0; i < 19; ++i) h[i] = A[RLB_CHK(i * S + idx + o.src(i), 38ll * S)];
         if (bounced) {
 #pragma unroll
             for (int i = 1; i < 19; ++i)
-                if ((bounced >> i) & 1u) h[i] = A[opp(i) * S + idx];
+                if ((bounced >> i) & 1u) h[i] = A[RLB_CHK(opp(i) * S + idx, 38ll * S)];
         }
         T muf[19];
         load_mu(muf, 0);
@@ -590,9 +590,9 @@ __global__ void __launch_bounds__(128, MINB)
                             r.my, r.mz, vE, vx, vy, vz);
         scatter_cell(muf, mug, aS, vE, vx, vy, vz, c, [&](int q, int i, T v) {
             if ((bounced >> i) & 1u)
-                Lout[(q - i + opp(i)) * S + idx] = v;
+                Lout[RLB_CHK((q - i + opp(i)) * S + idx, 38ll * S)] = v;
             else
-                Lout[q * S + idx + o.src(i)] = v;
+                Lout[RLB_CHK(q * S + idx + o.src(i), 38ll * S)] = v;
         });
         zero_to_ghost<T, XBC>(x, g.nx, idx, S, Lout);
     }
@@ -643,10 +643,10 @@ __global__ void __launch_bounds__(kStageThreads, 3)
         const uint32_t s0 = scol + 4u * (uint32_t)(slot * 38 * kStageThreads);
 #pragma unroll
         for (int i = 0; i < 19; ++i)
-            cp_async4(s0 + 4u * (uint32_t)(i * kStageThreads), A + (base + i) * S + cidx + o.src(i));
+            cp_async4(s0 + 4u * (uint32_t)(i * kStageThreads), RLB_CHK_PTR(A, (base + i) * S + cidx + o.src(i), 38ll * S));
 #pragma unroll
         for (int i = 0; i < 19; ++i)
-            cp_async4(s0 + 4u * (uint32_t)((19 + i) * kStageThreads), Lin + (base + i) * S + cidx);
+            cp_async4(s0 + 4u * (uint32_t)((19 + i) * kStageThreads), RLB_CHK_PTR(Lin, (base + i) * S + cidx, 38ll * S));
     };
 
     float tau_acc = 0.0f;
@@ -693,7 +693,7 @@ __global__ void __launch_bounds__(kStageThreads, 3)
                     for (int i = 1; i < 19; ++i) {
                         if (is_solid(h[i])) {
                             bounced |= 1u << i;
-                            h[i] = A[(19 + opp(i)) * S + idx];
+                            h[i] = A[RLB_CHK((19 + opp(i)) * S + idx, 38ll * S)];
                         }
                     }
                 }
@@ -701,7 +701,7 @@ __global__ void __launch_bounds__(kStageThreads, 3)
                 for (int i = 0; i < 19; ++i) mug[i] = sval(sg, 19 + i);
                 if (dup) {
 #pragma unroll
-                    for (int i = 0; i < 19; ++i) mug[i] += Lin[(19 + i) * S + idx + dup];
+                    for (int i = 0; i < 19; ++i) mug[i] += Lin[RLB_CHK((19 + i) * S + idx + dup, 38ll * S)];
                 }
                 cell_g(h, mug, c, r);
             }
@@ -715,8 +715,8 @@ __global__ void __launch_bounds__(kStageThreads, 3)
         } else if (solid) {  // never updated: identity
 #pragma unroll
             for (int i = 0; i < 19; ++i) {
-                Lout[i * S + idx] = sval(sf, 19 + i);
-                Lout[(19 + i) * S + idx] = sval(sg, 19 + i);
+                Lout[RLB_CHK(i * S + idx, 38ll * S)] = sval(sf, 19 + i);
+                Lout[RLB_CHK((19 + i) * S + idx, 38ll * S)] = sval(sg, 19 + i);
             }
         } else {
             float h[19], muf[19];
@@ -725,13 +725,13 @@ __global__ void __launch_bounds__(kStageThreads, 3)
             if (bounced) {
 #pragma unroll
                 for (int i = 1; i < 19; ++i)
-                    if ((bounced >> i) & 1u) h[i] = A[opp(i) * S + idx];
+                    if ((bounced >> i) & 1u) h[i] = A[RLB_CHK(opp(i) * S + idx, 38ll * S)];
             }
 #pragma unroll
             for (int i = 0; i < 19; ++i) muf[i] = sval(sf, 19 + i);
             if (dup) {
 #pragma unroll
-                for (int i = 0; i < 19; ++i) muf[i] += Lin[i * S + idx + dup];
+                for (int i = 0; i < 19; ++i) muf[i] += Lin[RLB_CHK(i * S + idx + dup, 38ll * S)];
             }
             float tf, aS, fbx, fby, fbz;
             cell_f(h, muf, r, c, tf, aS, fbx, fby, fbz);
@@ -741,9 +741,9 @@ __global__ void __launch_bounds__(kStageThreads, 3)
                                     r.bz, r.mx, r.my, r.mz, vE, vx, vy, vz);
             scatter_cell(muf, mug, aS, vE, vx, vy, vz, c, [&](int q, int i, float v) {
                 if ((bounced >> i) & 1u)
-                    Lout[(q - i + opp(i)) * S + idx] = v;
+                    Lout[RLB_CHK((q - i + opp(i)) * S + idx, 38ll * S)] = v;
                 else
-                    Lout[q * S + idx + o.src(i)] = v;
+                    Lout[RLB_CHK(q * S + idx + o.src(i), 38ll * S)] = v;
             });
             zero_to_ghost<float, XBC>(x, g.nx, idx, S, Lout);
         }
@@ -786,12 +786,12 @@ __global__ void __launch_bounds__(128) k_adjoint_macro(const T* __restrict__ A, 
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= g.N) return;
     const long long S = g.S;
-    if (is_solid(A[idx])) {
-        for (int q = 0; q < 38; ++q) lam[q * S + idx] = (T)0;
+    if (is_solid(A[RLB_CHK(idx, 38ll * S)])) {
+        for (int q = 0; q < 38; ++q) lam[RLB_CHK(q * S + idx, 38ll * S)] = (T)0;
         return;
     }
     double h[38];
-    for (int q = 0; q < 38; ++q) h[q] = (double)A[q * S + idx];
+    for (int q = 0; q < 38; ++q) h[q] = (double)A[RLB_CHK(q * S + idx, 38ll * S)];
     double sf = 0, E = 0, Mx = 0, My = 0, Mz = 0;
     for (int i = 0; i < 19; ++i) {
         sf += h[i];
@@ -822,8 +822,8 @@ __global__ void __launch_bounds__(128) k_adjoint_macro(const T* __restrict__ A, 
     double vE, vx, vy, vz;
     recovery_adjoint<double>(deps[idx], abx, aby, abz, E, sq, D, bx, by, bz, Mx, My, Mz, vE, vx, vy, vz);
     for (int i = 0; i < 19; ++i) {
-        lam[i * S + idx] = (T)aS;
-        lam[(19 + i) * S + idx] = (T)(vE + ph.c_l * (vel_x(i) * vx + vel_y(i) * vy + vel_z(i) * vz));
+        lam[RLB_CHK(i * S + idx, 38ll * S)] = (T)aS;
+        lam[RLB_CHK((19 + i) * S + idx, 38ll * S)] = (T)(vE + ph.c_l * (vel_x(i) * vx + vel_y(i) * vy + vel_z(i) * vz));
     }
 }
 
@@ -842,11 +842,11 @@ __global__ void __launch_bounds__(128) k_adjoint_fields(const double* __restrict
         const int x = idx % g.nx;
         double lf[19], lg[19];
         double an = 0, ae = 0, ax = 0, ay = 0, az = 0;
-        const bool solid = is_solid(A0[idx]);
+        const bool solid = is_solid(A0[RLB_CHK(idx, 38ll * S)]);
         if (!solid) {
             for (int i = 0; i < 19; ++i) {
-                lf[i] = (double)lam[i * S + idx];
-                lg[i] = (double)lam[(19 + i) * S + idx];
+                lf[i] = (double)lam[RLB_CHK(i * S + idx, 38ll * S)];
+                lg[i] = (double)lam[RLB_CHK((19 + i) * S + idx, 38ll * S)];
             }
             if (g.xbc == XBC_INFLOW_OUTFLOW && x == 0) {
                 eq_fields_adjoint(lf, lg, ph.n_in, ph.eps_in, ph.beta_in[0], ph.beta_in[1], ph.beta_in[2], ph, an,
@@ -1075,5 +1075,8 @@ cudaError_t launch_adjoint_step_noalloc(int prec, const Geom& g, const Phys& ph,
     k_finalize<<<1, 1024, 0, st>>>(red, grid * 4, dtau, dbeta_in);
     return cudaGetLastError();
 }
+
+// Bounds-check count of this translation unit (0 in the release build).
+RLB_OOB_TAKE_FN(oob_take_adjoint)
 
 }  // namespace rlb

@@ -577,6 +577,36 @@ rlb_status rlb_selftest_conversions(const float* f_in, const double* d_in, int64
     return RLB_OK;
 }
 
+rlb_status rlb_debug_bounds_violations(int64_t* count) {
+    if (!count) return fail(nullptr, RLB_ERR_ARG, "count is NULL");
+#ifdef RLB_CHECK_BOUNDS
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaDeviceSynchronize");
+    const unsigned long long a = oob_take_forward(), b = oob_take_adjoint(), d = oob_take_eos(), e2 = oob_take_stream();
+    if (a == ~0ull || b == ~0ull || d == ~0ull || e2 == ~0ull) return fail(nullptr, RLB_ERR_CUDA, "reading the bounds counters failed");
+    *count = (int64_t)(a + b + d + e2);
+    return RLB_OK;
+#else
+    *count = -1;
+    return fail(nullptr, RLB_ERR_STATE, "librlb was built without RLB_CHECK_BOUNDS");
+#endif
+}
+
+rlb_status rlb_debug_bounds_selftest(int64_t index, int64_t n, int64_t* checked) {
+    if (!checked) return fail(nullptr, RLB_ERR_ARG, "checked is NULL");
+#ifdef RLB_CHECK_BOUNDS
+    *checked = (int64_t)bounds_selftest((long long)index, (long long)n, 0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "bounds self-test");
+    return RLB_OK;
+#else
+    (void)index;
+    (void)n;
+    *checked = -1;
+    return fail(nullptr, RLB_ERR_STATE, "librlb was built without RLB_CHECK_BOUNDS");
+#endif
+}
+
 rlb_status rlb_sync(rlb_ctx* c) {
     RLB_LATCHED(c);
     RLB_CUDA(c, cudaStreamSynchronize(c->stream), "sync");

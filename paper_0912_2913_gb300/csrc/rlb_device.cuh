@@ -160,6 +160,51 @@ __device__ __forceinline__ void moments_pairs(const T* f, const T* g, T& sf, T& 
     mz = d[2] + d[5] - d[6] + d[7] - d[8];
 }
 
+// Optional bounds checking (a debug build, -DRLB_CHECK_BOUNDS): every
+// element index into a state buffer (38 S elements) in the step, adjoint and
+// equation-of-state kernels goes through RLB_CHK; an index outside the buffer
+// is counted (per translation unit) and replaced by an in-range one, so the
+// access itself stays inside the buffer.  The release build compiles the
+// indices unchanged.  RLB_CHK_OFF checks base + off and returns off;
+// RLB_CHK_PTR(p, e, n) is the pointer p + e with e checked.
+#ifdef RLB_CHECK_BOUNDS
+static __device__ unsigned long long g_rlb_oob_count;
+template <typename I>
+__device__ __forceinline__ I rlb_chk(I i, long long n) {
+    if (i < 0 || (long long)i >= n) {
+        atomicAdd(&g_rlb_oob_count, 1ull);
+        return (I)0;
+    }
+    return i;
+}
+template <typename I>
+__device__ __forceinline__ I rlb_chk_off(I off, long long base, long long n) {
+    if (base + (long long)off < 0 || base + (long long)off >= n) {
+        atomicAdd(&g_rlb_oob_count, 1ull);
+        return (I)(-base);
+    }
+    return off;
+}
+#define RLB_CHK(i, n) rlb_chk((i), (long long)(n))
+#define RLB_CHK_OFF(off, base, n) rlb_chk_off((off), (long long)(base), (long long)(n))
+#define RLB_CHK_PTR(p, e, n) ((p) + rlb_chk((e), (long long)(n)))
+// Host side, per translation unit: read and clear the count.
+#define RLB_OOB_TAKE_FN(name)                                                              \
+    unsigned long long name() {                                                            \
+        unsigned long long v = 0, z = 0;                                                   \
+        if (cudaMemcpyFromSymbol(&v, g_rlb_oob_count, sizeof v) != cudaSuccess) return ~0ull; \
+        cudaMemcpyToSymbol(g_rlb_oob_count, &z, sizeof z);                                 \
+        return v;                                                                          \
+    }
+#else
+#define RLB_CHK(i, n) (i)
+#define RLB_CHK_OFF(off, base, n) (off)
+// Expands to the unbracketed tokens p + e, so pointer arithmetic groups as written.
+#define RLB_CHK_PTR(p, e, n) p + e
+#define RLB_OOB_TAKE_FN(name) \
+    unsigned long long name() { return 0; }
+#endif
+
 // Cell coordinates by multiply-high division with host-computed magic
 // numbers (division by an invariant integer, Granlund and Montgomery 1994).
 __device__ __forceinline__ unsigned fast_div(unsigned n, const FastDiv& d) {

@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(128) k_step_eos(const double* __restrict__ A, 
         // ghost planes are not collided (the inflow plane is copied so that
         // every cell of B is written; outflow ghosts are written below)
         if (XBC == XBC_INFLOW_OUTFLOW && x == 0) {
-            for (int q = 0; q < 38; ++q) B[q * S + idx] = A[q * S + idx];
+            for (int q = 0; q < 38; ++q) B[RLB_CHK(q * S + idx, 38ll * S)] = A[RLB_CHK(q * S + idx, 38ll * S)];
         }
         return;
     }
@@ -140,19 +140,19 @@ __global__ void __launch_bounds__(128) k_step_eos(const double* __restrict__ A, 
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
         const int s = idx + o.src(i);
-        f[i] = A[i * S + s];
-        gg[i] = A[(19 + i) * S + s];
+        f[i] = A[RLB_CHK(i * S + s, 38ll * S)];
+        gg[i] = A[RLB_CHK((19 + i) * S + s, 38ll * S)];
     }
     if (is_solid(f[0])) {  // the cell itself is solid: keep the marker
         const double m = solid_marker_d();
-        for (int q = 0; q < 38; ++q) B[q * S + idx] = m;
+        for (int q = 0; q < 38; ++q) B[RLB_CHK(q * S + idx, 38ll * S)] = m;
         return;
     }
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
         if (is_solid(f[i])) {  // link bounce-back
-            f[i] = A[opp(i) * S + idx];
-            gg[i] = A[(19 + opp(i)) * S + idx];
+            f[i] = A[RLB_CHK(opp(i) * S + idx, 38ll * S)];
+            gg[i] = A[RLB_CHK((19 + opp(i)) * S + idx, 38ll * S)];
         }
     }
     double sf, E, mx, my, mz;
@@ -174,19 +174,19 @@ __global__ void __launch_bounds__(128) k_step_eos(const double* __restrict__ A, 
     }
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
-        B[i * S + idx] = f[i];
-        B[(19 + i) * S + idx] = gg[i];
+        B[RLB_CHK(i * S + idx, 38ll * S)] = f[i];
+        B[RLB_CHK((19 + i) * S + idx, 38ll * S)] = gg[i];
     }
     if (XBC != XBC_PERIODIC && x == g.nx - 2) {  // outflow ghost x = nx-1 copies x = nx-2
         for (int i = 0; i < 19; ++i) {
-            B[i * S + idx + 1] = f[i];
-            B[(19 + i) * S + idx + 1] = gg[i];
+            B[RLB_CHK(i * S + idx + 1, 38ll * S)] = f[i];
+            B[RLB_CHK((19 + i) * S + idx + 1, 38ll * S)] = gg[i];
         }
     }
     if (XBC == XBC_OUTFLOW_BOTH && x == 1) {  // outflow ghost x = 0 copies x = 1
         for (int i = 0; i < 19; ++i) {
-            B[i * S + idx - 1] = f[i];
-            B[(19 + i) * S + idx - 1] = gg[i];
+            B[RLB_CHK(i * S + idx - 1, 38ll * S)] = f[i];
+            B[RLB_CHK((19 + i) * S + idx - 1, 38ll * S)] = gg[i];
         }
     }
     if (count) count_flags(cnt, unphys, nonpos, (unsigned long long)step_index * (unsigned long long)g.N + idx);
@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(128) k_init_eos(const double* __restrict__ n, 
     const long long S = g.S;
     if (solid && solid[idx]) {
         const double m = solid_marker_d();
-        for (int q = 0; q < 38; ++q) A[q * S + idx] = B[q * S + idx] = m;
+        for (int q = 0; q < 38; ++q) A[RLB_CHK(q * S + idx, 38ll * S)] = B[RLB_CHK(q * S + idx, 38ll * S)] = m;
         return;
     }
     const int x = idx % g.nx;
@@ -212,8 +212,8 @@ __global__ void __launch_bounds__(128) k_init_eos(const double* __restrict__ n, 
         equilibrium_general(n[idx], eps[idx], eos_pressure(ph, n[idx], eps[idx]), beta[idx], beta[g.N + idx],
                             beta[2 * (long long)g.N + idx], ph, f, gg);
     for (int i = 0; i < 19; ++i) {
-        A[i * S + idx] = B[i * S + idx] = f[i];
-        A[(19 + i) * S + idx] = B[(19 + i) * S + idx] = gg[i];
+        A[RLB_CHK(i * S + idx, 38ll * S)] = B[RLB_CHK(i * S + idx, 38ll * S)] = f[i];
+        A[RLB_CHK((19 + i) * S + idx, 38ll * S)] = B[RLB_CHK((19 + i) * S + idx, 38ll * S)] = gg[i];
     }
 }
 
@@ -223,15 +223,15 @@ __global__ void __launch_bounds__(128) k_macro_eos(const double* __restrict__ A,
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= g.N) return;
     const long long S = g.S;
-    if (is_solid(A[idx])) {
+    if (is_solid(A[RLB_CHK(idx, 38ll * S)])) {
         const double nan = __longlong_as_double(0x7FF8000000000000ll);
         n[idx] = eps[idx] = beta[idx] = beta[g.N + idx] = beta[2 * (long long)g.N + idx] = nan;
         return;
     }
     double f[19], gg[19];
     for (int i = 0; i < 19; ++i) {
-        f[i] = A[i * S + idx];
-        gg[i] = A[(19 + i) * S + idx];
+        f[i] = A[RLB_CHK(i * S + idx, 38ll * S)];
+        gg[i] = A[RLB_CHK((19 + i) * S + idx, 38ll * S)];
     }
     double sf, E, mx, my, mz;
     moments_pairs(f, gg, sf, E, mx, my, mz);
@@ -286,5 +286,8 @@ cudaError_t launch_macro_eos(const Geom& g, const Phys& ph, const void* A, doubl
     k_macro_eos<<<nblocks(g.N, 128), 128, 0, st>>>((const double*)A, n, eps, beta, g, ph, cnt.macro_bad);
     return cudaGetLastError();
 }
+
+// Bounds-check count of this translation unit (0 in the release build).
+RLB_OOB_TAKE_FN(oob_take_eos)
 
 }  // namespace rlb

@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(128) k_step_f64(const double* __restrict__ A, 
         // ghosts are written by the cell they copy.
         if (XBC == XBC_INFLOW_OUTFLOW && x == 0) {
 #pragma unroll
-            for (int q = 0; q < 38; ++q) B[q * S + idx] = __ldg(A + q * S + idx);
+            for (int q = 0; q < 38; ++q) B[RLB_CHK(q * S + idx, 38ll * S)] = __ldg(RLB_CHK_PTR(A, q * S + idx, 38ll * S));
         }
         return;
     }
@@ -52,21 +52,21 @@ __global__ void __launch_bounds__(128) k_step_f64(const double* __restrict__ A, 
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
         const int s = idx + o.src(i);
-        f[i] = __ldg(A + i * S + s);
-        gg[i] = __ldg(A + (19 + i) * S + s);
+        f[i] = __ldg(RLB_CHK_PTR(A, i * S + s, 38ll * S));
+        gg[i] = __ldg(RLB_CHK_PTR(A, (19 + i) * S + s, 38ll * S));
     }
     if (SOLID) {
         if (is_solid(f[0])) {  // the cell itself is solid: keep the marker
             const double m = solid_marker_d();
 #pragma unroll
-            for (int q = 0; q < 38; ++q) B[q * S + idx] = m;
+            for (int q = 0; q < 38; ++q) B[RLB_CHK(q * S + idx, 38ll * S)] = m;
             return;
         }
 #pragma unroll
         for (int i = 1; i < 19; ++i) {
             if (is_solid(f[i])) {  // link bounce-back
-                f[i] = __ldg(A + opp(i) * S + idx);
-                gg[i] = __ldg(A + (19 + opp(i)) * S + idx);
+                f[i] = __ldg(RLB_CHK_PTR(A, opp(i) * S + idx, 38ll * S));
+                gg[i] = __ldg(RLB_CHK_PTR(A, (19 + opp(i)) * S + idx, 38ll * S));
             }
         }
     }
@@ -132,21 +132,21 @@ __global__ void __launch_bounds__(128) k_step_f64(const double* __restrict__ A, 
     }
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
-        B[i * S + idx] = outf[i];
-        B[(19 + i) * S + idx] = outg[i];
+        B[RLB_CHK(i * S + idx, 38ll * S)] = outf[i];
+        B[RLB_CHK((19 + i) * S + idx, 38ll * S)] = outg[i];
     }
     if (XBC != XBC_PERIODIC && x == g.nx - 2) {  // outflow ghost x = nx-1 copies x = nx-2
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
-            B[i * S + idx + 1] = outf[i];
-            B[(19 + i) * S + idx + 1] = outg[i];
+            B[RLB_CHK(i * S + idx + 1, 38ll * S)] = outf[i];
+            B[RLB_CHK((19 + i) * S + idx + 1, 38ll * S)] = outg[i];
         }
     }
     if (XBC == XBC_OUTFLOW_BOTH && x == 1) {  // outflow ghost x = 0 copies x = 1
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
-            B[i * S + idx - 1] = outf[i];
-            B[(19 + i) * S + idx - 1] = outg[i];
+            B[RLB_CHK(i * S + idx - 1, 38ll * S)] = outf[i];
+            B[RLB_CHK((19 + i) * S + idx - 1, 38ll * S)] = outg[i];
         }
     }
     if (count) count_flags(cnt, unphys, nonpos, (unsigned long long)step_index * (unsigned long long)g.N + idx);
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(256, MINB) k_step_f32(const float* __restrict_
     if (XBC != XBC_PERIODIC && (x == 0 || x == g.nx - 1)) {
         if (XBC == XBC_INFLOW_OUTFLOW && x == 0) {
 #pragma unroll
-            for (int q = 0; q < 38; ++q) B[q * S + idx] = __ldg(A + q * S + idx);
+            for (int q = 0; q < 38; ++q) B[RLB_CHK(q * S + idx, 38ll * S)] = __ldg(RLB_CHK_PTR(A, q * S + idx, 38ll * S));
         }
         return;
     }
@@ -196,21 +196,21 @@ __global__ void __launch_bounds__(256, MINB) k_step_f32(const float* __restrict_
     const int dup = (XBC != XBC_PERIODIC && x == g.nx - 2) ? 1 : ((XBC == XBC_OUTFLOW_BOTH && x == 1) ? -1 : 0);
     float* Bc = B + idx;
     auto put = [&](int q, float v) {
-        Bc[q * S] = v;
-        if (dup) Bc[q * S + dup] = v;
+        Bc[RLB_CHK_OFF(q * S, idx, 38ll * S)] = v;
+        if (dup) Bc[RLB_CHK_OFF(q * S + dup, idx, 38ll * S)] = v;
     };
-    if (SOLID && is_solid(__ldg(A + 19 * S + idx))) {  // the cell itself is solid: keep the marker
+    if (SOLID && is_solid(__ldg(RLB_CHK_PTR(A, 19 * S + idx, 38ll * S)))) {  // the cell itself is solid: keep the marker
         const float m = solid_marker_f();
 #pragma unroll
-        for (int q = 0; q < 38; ++q) Bc[q * S] = m;
+        for (int q = 0; q < 38; ++q) Bc[RLB_CHK_OFF(q * S, idx, 38ll * S)] = m;
         return;
     }
     if (PREF) {
 #pragma unroll
-        for (int i = 0; i < 19; ++i) asm volatile("prefetch.global.L2 [%0];" ::"l"(A + i * S + idx + o.src(i)));
+        for (int i = 0; i < 19; ++i) asm volatile("prefetch.global.L2 [%0];" ::"l"(RLB_CHK_PTR(A, i * S + idx + o.src(i), 38ll * S)));
     }
-    auto fetch = [&](int q, int i) { return __ldg(A + q * S + idx + o.src(i)); };
-    auto bounce = [&](int q, int i) { return __ldg(A + (q - i + opp(i)) * S + idx); };  // link bounce-back
+    auto fetch = [&](int q, int i) { return __ldg(RLB_CHK_PTR(A, q * S + idx + o.src(i), 38ll * S)); };
+    auto bounce = [&](int q, int i) { return __ldg(RLB_CHK_PTR(A, (q - i + opp(i)) * S + idx, 38ll * S)); };  // link bounce-back
     bool unphys, nonpos;
     collide_cell_f32<SOLID>(fetch, bounce, put, c, unphys, nonpos);
     if (count) count_flags(cnt, unphys, nonpos, (unsigned long long)step_index * (unsigned long long)g.N + idx);
@@ -233,8 +233,8 @@ __global__ void __launch_bounds__(256, 3) k_step_f32_pipe(const float* __restric
         const PullOffsets o(g, x, y, z);
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(A + (19 + i) * S + idx + o.src(i)));
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(A + i * S + idx + o.src(i)));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(RLB_CHK_PTR(A, (19 + i) * S + idx + o.src(i), 38ll * S)));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(RLB_CHK_PTR(A, i * S + idx + o.src(i), 38ll * S)));
         }
     };
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(256, 3) k_step_f32_pipe(const float* __restric
         if (XBC != XBC_PERIODIC && (x == 0 || x == g.nx - 1)) {
             if (XBC == XBC_INFLOW_OUTFLOW && x == 0) {
 #pragma unroll
-                for (int q = 0; q < 38; ++q) B[q * S + idx] = __ldg(A + q * S + idx);
+                for (int q = 0; q < 38; ++q) B[RLB_CHK(q * S + idx, 38ll * S)] = __ldg(RLB_CHK_PTR(A, q * S + idx, 38ll * S));
             }
             continue;
         }
@@ -258,18 +258,18 @@ __global__ void __launch_bounds__(256, 3) k_step_f32_pipe(const float* __restric
                 __stcs(Bc + q * S, v);
                 if (dup) __stcs(Bc + q * S + dup, v);
             } else {
-                Bc[q * S] = v;
-                if (dup) Bc[q * S + dup] = v;
+                Bc[RLB_CHK_OFF(q * S, idx, 38ll * S)] = v;
+                if (dup) Bc[RLB_CHK_OFF(q * S + dup, idx, 38ll * S)] = v;
             }
         };
-        if (SOLID && is_solid(__ldg(A + 19 * S + idx))) {
+        if (SOLID && is_solid(__ldg(RLB_CHK_PTR(A, 19 * S + idx, 38ll * S)))) {
             const float m = solid_marker_f();
 #pragma unroll
-            for (int q = 0; q < 38; ++q) Bc[q * S] = m;
+            for (int q = 0; q < 38; ++q) Bc[RLB_CHK_OFF(q * S, idx, 38ll * S)] = m;
             continue;
         }
-        auto fetch = [&](int q, int i) { return __ldg(A + q * S + idx + o.src(i)); };
-        auto bounce = [&](int q, int i) { return __ldg(A + (q - i + opp(i)) * S + idx); };
+        auto fetch = [&](int q, int i) { return __ldg(RLB_CHK_PTR(A, q * S + idx + o.src(i), 38ll * S)); };
+        auto bounce = [&](int q, int i) { return __ldg(RLB_CHK_PTR(A, (q - i + opp(i)) * S + idx, 38ll * S)); };
         bool unphys, nonpos;
         collide_cell_f32<SOLID>(fetch, bounce, put, c, unphys, nonpos);
         if (count) count_flags(cnt, unphys, nonpos, (unsigned long long)step_index * (unsigned long long)g.N + idx);
@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(128) k_init(const double* __restrict__ n, cons
     if (solid && solid[idx]) {
         T m;
         if constexpr (sizeof(T) == 8) m = solid_marker_d(); else m = solid_marker_f();
-        for (int q = 0; q < 38; ++q) A[q * S + idx] = B[q * S + idx] = m;
+        for (int q = 0; q < 38; ++q) A[RLB_CHK(q * S + idx, 38ll * S)] = B[RLB_CHK(q * S + idx, 38ll * S)] = m;
         return;
     }
     const int x = idx % g.nx;
@@ -342,8 +342,8 @@ __global__ void __launch_bounds__(128) k_init(const double* __restrict__ n, cons
         }
     }
     for (int i = 0; i < 19; ++i) {
-        A[i * S + idx] = B[i * S + idx] = (T)f[i];
-        A[(19 + i) * S + idx] = B[(19 + i) * S + idx] = (T)gg[i];
+        A[RLB_CHK(i * S + idx, 38ll * S)] = B[RLB_CHK(i * S + idx, 38ll * S)] = (T)f[i];
+        A[RLB_CHK((19 + i) * S + idx, 38ll * S)] = B[RLB_CHK((19 + i) * S + idx, 38ll * S)] = (T)gg[i];
     }
 }
 
@@ -359,15 +359,15 @@ __global__ void __launch_bounds__(128) k_macro(const T* __restrict__ A, double* 
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= g.N) return;
     const long long S = g.S;
-    if (is_solid(A[idx])) {
+    if (is_solid(A[RLB_CHK(idx, 38ll * S)])) {
         const double nan = __longlong_as_double(0x7FF8000000000000ll);
         n[idx] = eps[idx] = beta[idx] = beta[g.N + idx] = beta[2 * (long long)g.N + idx] = nan;
         return;
     }
     double f[19], gg[19];
     for (int i = 0; i < 19; ++i) {
-        f[i] = (double)A[i * S + idx];
-        gg[i] = (double)A[(19 + i) * S + idx];
+        f[i] = (double)A[RLB_CHK(i * S + idx, 38ll * S)];
+        gg[i] = (double)A[RLB_CHK((19 + i) * S + idx, 38ll * S)];
     }
     double sf, E, mx, my, mz;
     moments_pairs(f, gg, sf, E, mx, my, mz);
@@ -543,5 +543,24 @@ cudaError_t launch_check_solid_planes(const Geom& g, const uint8_t* solid, unsig
     k_check_solid_planes<<<blocks_for(n, 256), 256, 0, st>>>(g, solid, flag);
     return cudaGetLastError();
 }
+
+// Bounds-check count of this translation unit (0 in the release build).
+RLB_OOB_TAKE_FN(oob_take_forward)
+
+#ifdef RLB_CHECK_BOUNDS
+// The checker itself on one index (no memory is accessed with it): counts a
+// violation and returns 0 when the index lies outside [0, n).
+static __device__ long long g_rlb_chk_result;
+__global__ void k_bounds_selftest(long long i, long long n) { g_rlb_chk_result = RLB_CHK(i, n); }
+
+long long bounds_selftest(long long i, long long n, cudaStream_t s) {
+    k_bounds_selftest<<<1, 1, 0, s>>>(i, n);
+    long long r = -1;
+    if (cudaMemcpyFromSymbolAsync(&r, g_rlb_chk_result, sizeof r, 0, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return -1;
+    return r;
+}
+#endif
 
 }  // namespace rlb

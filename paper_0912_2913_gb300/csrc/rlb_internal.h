@@ -116,6 +116,17 @@ cudaError_t launch_step_eos(const Geom& g, const Phys& ph, const void* A, void* 
 cudaError_t launch_macro_eos(const Geom& g, const Phys& ph, const void* A, double* n, double* eps, double* beta,
                              Counters cnt, cudaStream_t stream);
 
+// Out-of-range state indices counted by the bounds-checking build since the
+// last call, per translation unit (always 0 in the release build).
+unsigned long long oob_take_forward();
+unsigned long long oob_take_adjoint();
+unsigned long long oob_take_eos();
+unsigned long long oob_take_stream();
+#ifdef RLB_CHECK_BOUNDS
+// Runs the index check on (i, n) in a kernel; returns the checked index.
+long long bounds_selftest(long long i, long long n, cudaStream_t s);
+#endif
+
 // Kernel launches issued by the last launcher call (for accounting).
 int last_launch_count();
 void set_last_launch_count(int n);

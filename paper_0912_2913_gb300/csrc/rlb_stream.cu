@@ -74,9 +74,9 @@ __global__ void __launch_bounds__(256, MINB)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int q = i + 19 * h;
-                bulk_g2s(st + q * plane_elems, A + q * S + row0, (unsigned)(seg * nx * 4), &bars[s]);
+                bulk_g2s(st + q * plane_elems, RLB_CHK_PTR(A, q * S + row0, 38ll * S), (unsigned)(seg * nx * 4), &bars[s]);
                 if (seg < rr)
-                    bulk_g2s(st + q * plane_elems + seg * nx, A + q * S + wrap0, (unsigned)((rr - seg) * nx * 4),
+                    bulk_g2s(st + q * plane_elems + seg * nx, RLB_CHK_PTR(A, q * S + wrap0, 38ll * S), (unsigned)((rr - seg) * nx * 4),
                              &bars[s]);
             }
         }
@@ -113,14 +113,14 @@ __global__ void __launch_bounds__(256, MINB)
             if (XBC != XBC_PERIODIC && (x == 0 || x == nx - 1)) {
                 if (XBC == XBC_INFLOW_OUTFLOW && x == 0) {
 #pragma unroll
-                    for (int q = 0; q < 38; ++q) B[q * S + idx] = __ldg(A + q * S + idx);
+                    for (int q = 0; q < 38; ++q) B[RLB_CHK(q * S + idx, 38ll * S)] = __ldg(RLB_CHK_PTR(A, q * S + idx, 38ll * S));
                 }
                 continue;
             }
             if (SOLID && is_solid(st[19 * plane_elems + r * nx + x])) {
                 const float m = solid_marker_f();
 #pragma unroll
-                for (int q = 0; q < 38; ++q) B[q * S + idx] = m;
+                for (int q = 0; q < 38; ++q) B[RLB_CHK(q * S + idx, 38ll * S)] = m;
                 continue;
             }
             const int xm = (x == 0) ? nx - 1 : x - 1;
@@ -130,12 +130,12 @@ __global__ void __launch_bounds__(256, MINB)
                 const int ex = vel_x(i);
                 return row[q * plane_elems + (ex > 0 ? xm : (ex < 0 ? xp : x))];
             };
-            auto bounce = [&](int q, int i) { return __ldg(A + (q - i + opp(i)) * S + idx); };  // link bounce-back
+            auto bounce = [&](int q, int i) { return __ldg(RLB_CHK_PTR(A, (q - i + opp(i)) * S + idx, 38ll * S)); };  // link bounce-back
             const int dup = (XBC != XBC_PERIODIC && x == nx - 2) ? 1 : ((XBC == XBC_OUTFLOW_BOTH && x == 1) ? -1 : 0);
             float* Bc = B + idx;
             auto put = [&](int q, float v) {
-                Bc[q * S] = v;
-                if (dup) Bc[q * S + dup] = v;
+                Bc[RLB_CHK_OFF(q * S, idx, 38ll * S)] = v;
+                if (dup) Bc[RLB_CHK_OFF(q * S + dup, idx, 38ll * S)] = v;
             };
             bool unphys, nonpos;
             collide_cell_f32<SOLID>(fetch, bounce, put, c, unphys, nonpos);
@@ -225,5 +225,8 @@ cudaError_t launch_step_f32_tma(const Geom& g, const Dev32& c, const float* A, f
     }
     return cudaGetLastError();
 }
+
+// Bounds-check count of this translation unit (0 in the release build).
+RLB_OOB_TAKE_FN(oob_take_stream)
 
 }  // namespace rlb

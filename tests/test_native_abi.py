@@ -91,3 +91,16 @@ def test_allocation_failure_is_reported(native, monkeypatch):
         N.rlb_create(N.make_params(16, 8, 4, 0.8), None, None, 0)
     assert ei.value.status == N.RLB_ERR_OOM
     assert "injected allocation failure" in N.rlb_last_error(None)
+
+
+def test_release_library_refuses_the_bounds_debug_calls(native):
+    """The bounds counters exist only in the -DRLB_CHECK_BOUNDS build; the
+    release library answers RLB_ERR_STATE without touching the GPU."""
+    N = native
+    if os.environ.get("RLB_LIBRARY_VARIANT", "release") != "release":
+        pytest.skip("the bounds build is loaded")
+    for call in (N.rlb_debug_bounds_violations, lambda: N.rlb_debug_bounds_selftest(1, 2)):
+        with pytest.raises(N.RLBError) as ei:
+            call()
+        assert ei.value.status == N.RLB_ERR_STATE
+        assert "RLB_CHECK_BOUNDS" in N.rlb_last_error(None)
