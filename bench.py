@@ -403,6 +403,57 @@ def shock_tube_graph_leg(device, steps_per_graph=100, replays=20):
             "mlups_graph": w.N / us_graph}
 
 
+def gradient_run_leg(w, T, device, ms_forward, budget_cap=200e9, reserve=40e9):
+    """One whole gradient evaluation through rlb_run (FP32, T steps, loss =
+    sum of P^2 = (eps/3)^2 over the plane x = 120, gradients for tau,
+    beta_in and the initial fields): forward and backward pass times, with
+    plain sqrt(T) checkpointing (K = 45) and with the last states of the run
+    kept within a device-memory budget (min(budget_cap, free - reserve)) so
+    fewer steps are recomputed.  ratio_to_forward = backward ms per step over
+    the forward step of the headline leg."""
+    import torch
+
+    from paper_0912_2913_gb300 import RunSpec, rlb_run
+
+    torch.cuda.empty_cache()
+    budget = max(0.0, min(budget_cap, torch.cuda.mem_get_info(device)[0] - reserve))
+    out = {"steps": T, "loss": "sum over the plane x = 120 of (eps/3)^2"}
+    for name, K, b in (("sqrt_t", 45, None), ("stored_tail", None, budget)):
+        spec = RunSpec.from_workload(w, "fp32", steps=T, checkpoint_every=K, store_budget_bytes=b, device=device)
+        try:
+            plan = spec.plan(38 * (-(-w.N // 64) * 64) * 4)
+        except ValueError as e:
+            out[name] = {"skipped": str(e)}
+            continue
+        f64 = dict(dtype=torch.float64, device=device)
+        tau = torch.tensor(w.tau, **f64, requires_grad=True)
+        bi = torch.tensor(w.beta_in, **f64, requires_grad=True)
+        n0, e0, b0 = (torch.from_numpy(np.ascontiguousarray(a)).to(device).requires_grad_(True)
+                      for a in (w.n, w.eps, w.beta))
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        torch.cuda.synchronize()
+        ev[0].record()
+        n, e, bb = rlb_run(tau, bi, n0, e0, b0, spec)
+        ev[1].record()
+        L = (e[:, :, 120] / 3.0).square().sum()
+        ev[2].record()
+        L.backward()
+        ev[3].record()
+        torch.cuda.synchronize()
+        fwd, bwd = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
+        plan = spec.last_plan
+        out[name] = {"forward_ms": fwd, "backward_ms": bwd, "backward_ms_per_step": bwd / T,
+                     "ratio_to_forward": (bwd / T) / ms_forward, "states_held": plan.states_held,
+                     "state_gb": plan.states_held * spec.last_sim.state_bytes / 1e9, "stored_tail": plan.P,
+                     "checkpoint_every": plan.K, "recomputed_steps": plan.recomputed_steps,
+                     "grad_finite": bool(torch.isfinite(tau.grad) and torch.isfinite(bi.grad).all()
+                                         and torch.isfinite(e0.grad).all())}
+        spec.last_sim.close()
+        del n, e, bb, L, tau, bi, n0, e0, b0, spec
+        torch.cuda.empty_cache()
+    return out
+
+
 def e2e_run(w, job_steps, jobs, device):
     """End to end through the public API: host fields -> rlb_init_fields
     (H2D) -> job_steps steps -> rlb_macro to host (D2H), FP32."""
@@ -501,6 +552,8 @@ def run_ours(args):
             sim.close()
             del sim
             torch.cuda.empty_cache()
+            if not args.no_adjoint and args.workload == "sphere" and args.grad_steps > 0:
+                legs["fp32_gradient_run"] = gradient_run_leg(w, args.grad_steps, device, ms / args.steps)
             sim = RLB.from_workload(w, "fp64", device=device).init_fields(w.n, w.eps, w.beta, w.solid)
             k64 = max(1, args.steps // 4)
             ms64, _ = time_forward(sim, k64, max(3, args.warmup // 4), 1, device)
@@ -624,6 +677,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--headline-only", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--grad-steps", type=int, default=2000,
+                    help="steps of the whole-gradient leg (rlb_run forward + backward); 0 skips it")
     ap.add_argument("--workload", choices=["sphere", "box512"], default="sphere")
     ap.add_argument("--profile", choices=["step", "adjoint", "box"], default=None,
                     help="short run of one kernel family for ncu captures (no JSON bench line)")

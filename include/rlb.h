@@ -142,6 +142,13 @@ RLB_API rlb_status rlb_step(rlb_ctx* ctx, int32_t nsteps);
  * written.  Does not touch the context's own state or its statistics.      */
 RLB_API rlb_status rlb_step_into(rlb_ctx* ctx, const void* src, void* dst);
 
+/* As rlb_step_into, and the update counts in the context's statistics as its
+ * next time step (steps, n_unphysical, first_bad, n_nonpositive_eq): a run
+ * that keeps its states in caller buffers (the stored tail of a checkpointed
+ * gradient run) reports the statistics of rlb_step.  The context's own state
+ * is not touched.  Not in the paper.                                        */
+RLB_API rlb_status rlb_step_into_counted(rlb_ctx* ctx, const void* src, void* dst);
+
 /* Device pointer of the context's current state (valid until the next
  * rlb_step / rlb_init_fields / rlb_load_state / rlb_destroy).               */
 RLB_API rlb_status rlb_state_ptr(rlb_ctx* ctx, void** state);

@@ -24,7 +24,7 @@ RLB_EOS_ULTRA, RLB_EOS_GAMMA_LAW = 0, 1
 # Every symbol include/rlb.h declares.
 EXPORTS = (
     "rlb_state_layout", "rlb_workspace_bytes", "rlb_create", "rlb_destroy", "rlb_init_fields", "rlb_step",
-    "rlb_step_into", "rlb_state_ptr", "rlb_save_state", "rlb_load_state", "rlb_macro", "rlb_stats",
+    "rlb_step_into", "rlb_step_into_counted", "rlb_state_ptr", "rlb_save_state", "rlb_load_state", "rlb_macro", "rlb_stats",
     "rlb_adjoint_macro", "rlb_adjoint_step", "rlb_adjoint_fields", "rlb_sync", "rlb_status_str", "rlb_last_error",
     "rlb_launch_count", "rlb_selftest_conversions", "rlb_adjoint_step_noalloc", "rlb_debug_bounds_violations",
     "rlb_debug_bounds_selftest",
@@ -90,6 +90,7 @@ def load(build_if_missing: bool = True):
             "rlb_init_fields": ([vp, dp, dp, dp, vp, ctypes.c_int], st),
             "rlb_step": ([vp, i32], st),
             "rlb_step_into": ([vp, vp, vp], st),
+            "rlb_step_into_counted": ([vp, vp, vp], st),
             "rlb_state_ptr": ([vp, P(vp)], st),
             "rlb_save_state": ([vp, vp], st),
             "rlb_load_state": ([vp, vp], st),
@@ -185,6 +186,10 @@ def rlb_step(ctx, nsteps: int) -> None:
 
 def rlb_step_into(ctx, src, dst) -> None:
     _check(load().rlb_step_into(ctx, _ptr(src), _ptr(dst)), ctx)
+
+
+def rlb_step_into_counted(ctx, src, dst) -> None:
+    _check(load().rlb_step_into_counted(ctx, _ptr(src), _ptr(dst)), ctx)
 
 
 def rlb_state_ptr(ctx) -> int:

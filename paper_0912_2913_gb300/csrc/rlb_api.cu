@@ -424,6 +424,21 @@ rlb_status rlb_step_into(rlb_ctx* c, const void* src, void* dst) {
                         "step_into");
 }
 
+rlb_status rlb_step_into_counted(rlb_ctx* c, const void* src, void* dst) {
+    Nvtx nvtx_("rlb_step_into_counted");
+    RLB_LATCHED(c);
+    if (!src || !dst || src == dst) return fail(c, RLB_ERR_ARG, "src and dst must be distinct device buffers");
+    if (!c->inited) return fail(c, RLB_ERR_STATE, "rlb_step_into_counted before rlb_init_fields");
+    if (c->g.variant < 0) c->g.variant = 1;
+    rlb_status s = after_launch(c,
+                                c->ph.eos ? launch_step_eos(c->g, c->ph, src, dst, c->cnt, true, c->steps, c->stream)
+                                          : launch_step(c->p.prec, c->g, c->ph, src, dst, c->cnt, true, c->steps,
+                                                        c->stream),
+                                "step_into_counted");
+    if (s == RLB_OK) c->steps += 1;
+    return s;
+}
+
 rlb_status rlb_state_ptr(rlb_ctx* c, void** state) {
     RLB_LATCHED(c);
     if (!state) return fail(c, RLB_ERR_ARG, "state is NULL");

@@ -112,8 +112,10 @@ class RLB:
         N.rlb_step(self.ctx, nsteps)
         return self
 
-    def step_into(self, src: torch.Tensor, dst: torch.Tensor):
-        N.rlb_step_into(self.ctx, src, dst)
+    def step_into(self, src: torch.Tensor, dst: torch.Tensor, counted: bool = False):
+        """One step from src into dst (caller states); counted=True adds it to
+        the context's statistics as its next step."""
+        (N.rlb_step_into_counted if counted else N.rlb_step_into)(self.ctx, src, dst)
 
     def save_state(self, dst: torch.Tensor):
         N.rlb_save_state(self.ctx, dst)

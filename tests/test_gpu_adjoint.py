@@ -362,3 +362,38 @@ def test_sphere_gradient_full_size_2000_steps():
     """The adjoint 3D sphere at full size: 200x100x100, 2000 steps (45
     checkpoints of 45 steps), plane x = 120."""
     _sphere_gradient_check(200, 100, 100, 2000, 120)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_stored_tail_gives_the_same_gradient(prec):
+    """rlb_run with a device-memory budget (the last states of the run kept
+    from the forward pass, the rest checkpointed) gives the outputs and
+    gradients of plain sqrt(T) checkpointing bit for bit, and the context
+    counts all T steps."""
+    from paper_0912_2913_gb300 import RLB, RunSpec, rlb_run
+
+    w = tiny_workload(37, 9, 5, 1, seed=21, solid_cells=((12, 4, 2), (13, 4, 2)))
+    T = 30
+    probe = RLB.from_workload(w, prec, device="cuda:0")
+    state_bytes = probe.state_bytes
+    probe.close()
+    out = []
+    for budget, expect in ((None, "plain"), (16 * state_bytes, "mixed"), (T * 2 * state_bytes, "all")):
+        spec = RunSpec.from_workload(w, prec, steps=T, store_budget_bytes=budget)
+        dev = "cuda:0"
+        tau = torch.tensor(w.tau, dtype=torch.float64, device=dev, requires_grad=True)
+        bi = torch.tensor(w.beta_in, dtype=torch.float64, device=dev, requires_grad=True)
+        n0, e0, b0 = (torch.from_numpy(np.ascontiguousarray(a)).to(dev).requires_grad_(True)
+                      for a in (w.n, w.eps, w.beta))
+        n, e, b = rlb_run(tau, bi, n0, e0, b0, spec)
+        m = torch.from_numpy(w.solid == 0).to(dev)
+        L = torch.where(m, e * e + 0.5 * n, torch.zeros_like(e)).sum() + torch.where(m, b[0], torch.zeros_like(e)).sum()
+        L.backward()
+        plan = spec.last_plan
+        assert {"plain": plan.P == 0, "mixed": plan.P > 0 and plan.H > 0, "all": plan.H == 0}[expect], vars(plan)
+        assert plan.states_held <= (budget // state_bytes if budget else plan.states_held)
+        assert spec.last_sim.stats()["steps"] == T
+        out.append([t.detach().clone() for t in (n, e, b, tau.grad, bi.grad, n0.grad, e0.grad, b0.grad)])
+    for other in out[1:]:
+        for a, b in zip(out[0], other):
+            assert torch.equal(torch.nan_to_num(a, nan=7.0), torch.nan_to_num(b, nan=7.0))
