@@ -417,11 +417,13 @@ def gradient_run_leg(w, T, device, ms_forward, budget_cap=200e9, reserve=40e9):
 
     torch.cuda.empty_cache()
     budget = max(0.0, min(budget_cap, torch.cuda.mem_get_info(device)[0] - reserve))
-    out = {"steps": T, "loss": "sum over the plane x = 120 of (eps/3)^2"}
-    for name, K, b in (("sqrt_t", 45, None), ("stored_tail", None, budget)):
-        spec = RunSpec.from_workload(w, "fp32", steps=T, checkpoint_every=K, store_budget_bytes=b, device=device)
+    out = {"steps": T, "loss": "sum over the plane x = 120 of (eps/3)^2",
+           "warmup": "one untimed 20-step gradient run of each kind first"}
+    for name, K, b, TT in (("warmup", 5, None, 20), ("warmup", None, 1e30, 20), ("sqrt_t", 45, None, T),
+                           ("stored_tail", None, budget, T)):
+        spec = RunSpec.from_workload(w, "fp32", steps=TT, checkpoint_every=K, store_budget_bytes=b, device=device)
         try:
-            plan = spec.plan(38 * (-(-w.N // 64) * 64) * 4)
+            spec.plan(38 * (-(-w.N // 64) * 64) * 4)
         except ValueError as e:
             out[name] = {"skipped": str(e)}
             continue
@@ -442,6 +444,9 @@ def gradient_run_leg(w, T, device, ms_forward, budget_cap=200e9, reserve=40e9):
         torch.cuda.synchronize()
         fwd, bwd = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
         plan = spec.last_plan
+        if name == "warmup":
+            spec.last_sim.close()
+            continue
         out[name] = {"forward_ms": fwd, "backward_ms": bwd, "backward_ms_per_step": bwd / T,
                      "ratio_to_forward": (bwd / T) / ms_forward, "states_held": plan.states_held,
                      "state_gb": plan.states_held * spec.last_sim.state_bytes / 1e9, "stored_tail": plan.P,

@@ -457,7 +457,7 @@ __device__ __forceinline__ void scatter_cell(const T* muf, const T* mug, T aS, T
 template <typename T, int XBC>
 __device__ __forceinline__ void ghost_cell(int x, int idx, long long S, const T* __restrict__ A,
                                            const T* __restrict__ Lin, T* __restrict__ Lout,
-                                           const double* __restrict__ inflow_d, double& bin0, double& bin1,
+                                           const T* __restrict__ inflow_t, double& bin0, double& bin1,
                                            double& bin2, bool& has_b) {
     const int inward = (x == 0) ? 1 : -1;
 #pragma unroll
@@ -472,9 +472,9 @@ __device__ __forceinline__ void ghost_cell(int x, int idx, long long S, const T*
 #pragma unroll 2
         for (int q = 0; q < 38; ++q) {
             const T l = Lin[RLB_CHK(q * S + idx, 38ll * S)];
-            a0 += l * (T)inflow_d[3 * q + 0];
-            a1 += l * (T)inflow_d[3 * q + 1];
-            a2 += l * (T)inflow_d[3 * q + 2];
+            a0 += l * inflow_t[3 * q + 0];
+            a1 += l * inflow_t[3 * q + 1];
+            a2 += l * inflow_t[3 * q + 2];
         }
         bin0 += (double)a0;
         bin1 += (double)a1;
@@ -509,7 +509,7 @@ __device__ __forceinline__ int dup_of(int x, int nx) {
 template <typename T, int XBC, int MINB, bool PIPE>
 __global__ void __launch_bounds__(128, MINB)
     k_adjoint_step(const T* __restrict__ A, const T* __restrict__ Lin, T* __restrict__ Lout, Geom g, Phys ph,
-                   AdjConst<T> c, double* red, const double* __restrict__ inflow_d) {
+                   AdjConst<T> c, double* red, const T* __restrict__ inflow_t) {
     const long long S = g.S;
     T tau_acc = 0;
     double bin0 = 0.0, bin1 = 0.0, bin2 = 0.0;
@@ -521,7 +521,7 @@ __global__ void __launch_bounds__(128, MINB)
         int x, y, z;
         cell_coords(g, idx, x, y, z);
         if ((XBC != XBC_PERIODIC) && (x == 0 || x == g.nx - 1)) {
-            ghost_cell<T, XBC>(x, idx, S, A, Lin, Lout, inflow_d, bin0, bin1, bin2, has_b);
+            ghost_cell<T, XBC>(x, idx, S, A, Lin, Lout, inflow_t, bin0, bin1, bin2, has_b);
             continue;
         }
         if (is_solid(A[RLB_CHK(19 * S + idx, 38ll * S)])) {  // never updated: identity
@@ -630,7 +630,7 @@ __device__ __forceinline__ void cp_async_wait() {
 template <int XBC, typename I>
 __global__ void __launch_bounds__(kStageThreads, 3)
     k_adjoint_step_staged(const float* __restrict__ A, const float* __restrict__ Lin, float* __restrict__ Lout,
-                          Geom g, Phys ph, AdjConst<float> c, double* red, const double* __restrict__ inflow_d) {
+                          Geom g, Phys ph, AdjConst<float> c, double* red, const float* __restrict__ inflow_t) {
     extern __shared__ float stage[];  // [slot][value 0..37][thread]
     const I S = (I)g.S;
     const int tid = threadIdx.x;
@@ -711,7 +711,7 @@ __global__ void __launch_bounds__(kStageThreads, 3)
         cp_async_wait<1>();  // F_k has landed
         // ---- f phase, scatter
         if (ghost) {
-            ghost_cell<float, XBC>(x, idx, S, A, Lin, Lout, inflow_d, bin0, bin1, bin2, has_b);
+            ghost_cell<float, XBC>(x, idx, S, A, Lin, Lout, inflow_t, bin0, bin1, bin2, has_b);
         } else if (solid) {  // never updated: identity
 #pragma unroll
             for (int i = 0; i < 19; ++i) {
@@ -756,7 +756,8 @@ __global__ void __launch_bounds__(kStageThreads, 3)
 }
 
 // d eq_j(n_in, eps_in, beta_in) / d beta_in,a for the 38 populations (one
-// thread per population, FP64): the adjoint of the inflow plane.
+// thread per population, FP64): the adjoint of the inflow plane.  The table
+// is written twice: binary64, then rounded to binary32 after it.
 __global__ void k_inflow_derivs(Phys ph, double* out) {
     const int j = threadIdx.x;
     if (j >= 38) return;
@@ -768,6 +769,19 @@ __global__ void k_inflow_derivs(Phys ph, double* out) {
     out[3 * j + 0] = ax;
     out[3 * j + 1] = ay;
     out[3 * j + 2] = az;
+    float* outf = reinterpret_cast<float*>(out + kInflowTable);
+    outf[3 * j + 0] = (float)ax;
+    outf[3 * j + 1] = (float)ay;
+    outf[3 * j + 2] = (float)az;
+}
+
+// The inflow table in the kernels' precision.
+template <typename T>
+const T* inflow_table(const double* inflow_d) {
+    if constexpr (sizeof(T) == 8)
+        return inflow_d;
+    else
+        return reinterpret_cast<const float*>(inflow_d + kInflowTable);
 }
 
 cudaError_t launch_inflow_derivs(const Phys& ph, double* out, cudaStream_t st) {
@@ -889,6 +903,7 @@ template <typename T>
 static int adjoint_step_t(const Geom& g, const Phys& ph, const T* A, const T* Li, T* Lo, double* red, int nb,
                           const double* inflow_d, cudaStream_t st) {
     const AdjConst<T> c = make_adj_const<T>(ph);
+    const T* inflow_t = inflow_table<T>(inflow_d);
     auto persistent_grid = [&](int minb) {
         static int nsm = 0;
         if (nsm == 0) {
@@ -902,7 +917,7 @@ static int adjoint_step_t(const Geom& g, const Phys& ph, const T* A, const T* Li
     // each launcher returns the number of warps whose partial sums it wrote
     auto go = [&](auto kern, bool pipe, int minb) {
         const int grid = pipe ? persistent_grid(minb) : nb;
-        kern<<<grid, 128, 0, st>>>(A, Li, Lo, g, ph, c, red, inflow_d);
+        kern<<<grid, 128, 0, st>>>(A, Li, Lo, g, ph, c, red, inflow_t);
         return grid * 4;
     };
     int warps = 0;
@@ -920,7 +935,7 @@ static int adjoint_step_t(const Geom& g, const Phys& ph, const T* A, const T* Li
                     attr[dev][which] = 1;
                 }
                 const int grid = persistent_grid(3);
-                kern<<<grid, kStageThreads, kStageSmemBytes, st>>>(A, Li, Lo, g, ph, c, red, inflow_d);
+                kern<<<grid, kStageThreads, kStageSmemBytes, st>>>(A, Li, Lo, g, ph, c, red, inflow_t);
                 return grid * (kStageThreads / 32);
             };
             if (idx32) {
@@ -1031,17 +1046,18 @@ template <typename T, int MINB>
 int adjoint_step_noalloc_t(const Geom& g, const Phys& ph, const T* A, const T* Li, T* Lo, double* red, int grid,
                            const double* inflow_d, cudaStream_t st) {
     const AdjConst<T> c = make_adj_const<T>(ph);
+    const T* inflow_t = inflow_table<T>(inflow_d);
     switch (g.xbc) {
         case XBC_PERIODIC:
-            k_adjoint_step<T, XBC_PERIODIC, MINB, true><<<grid, 128, 0, st>>>(A, Li, Lo, g, ph, c, red, inflow_d);
+            k_adjoint_step<T, XBC_PERIODIC, MINB, true><<<grid, 128, 0, st>>>(A, Li, Lo, g, ph, c, red, inflow_t);
             break;
         case XBC_INFLOW_OUTFLOW:
             k_adjoint_step<T, XBC_INFLOW_OUTFLOW, MINB, true><<<grid, 128, 0, st>>>(A, Li, Lo, g, ph, c, red,
-                                                                                   inflow_d);
+                                                                                   inflow_t);
             break;
         default:
             k_adjoint_step<T, XBC_OUTFLOW_BOTH, MINB, true><<<grid, 128, 0, st>>>(A, Li, Lo, g, ph, c, red,
-                                                                                 inflow_d);
+                                                                                 inflow_t);
             break;
     }
     return grid;

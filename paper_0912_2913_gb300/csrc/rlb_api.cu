@@ -30,7 +30,7 @@ struct rlb_ctx {
     void* B;  // the other buffer
     Counters cnt;
     double* red;  // adjoint partial sums
-    double* inflow_d;  // d eq_in / d beta_in, 38 x 3
+    double* inflow_d;  // d eq_in / d beta_in, 38 x 3 doubles, then the same as floats
     size_t state_bytes;
     int elem;
     int64_t steps;
@@ -123,7 +123,7 @@ void layout(const rlb_params* p, long long* S, int* elem, size_t* state_bytes) {
 }
 
 size_t counters_bytes() {
-    return align_up(sizeof(unsigned long long) * (2 * kCounterSlots + 3), kAlign) + align_up(sizeof(double) * 38 * 3, kAlign);
+    return align_up(sizeof(unsigned long long) * (2 * kCounterSlots + 3), kAlign) + align_up((sizeof(double) + sizeof(float)) * kInflowTable, kAlign);
 }
 size_t red_bytes(const rlb_params* p) {
     return align_up(sizeof(double) * adj_red_doubles((long long)p->nx * p->ny * p->nz), kAlign);

@@ -101,7 +101,10 @@ constexpr long long kAdjScratchDoubles = 32768;  // 256 KiB
 cudaError_t launch_adjoint_step_noalloc(int prec, const Geom& g, const Phys& ph, const void* A, const void* lam_in,
                                         void* lam_out, const double* inflow_d, double* dtau, double* dbeta_in,
                                         cudaStream_t stream, long long* need_doubles);
-// d eq_in / d beta_in table (38 x 3 doubles) of the inflow state.
+// d eq_in / d beta_in table of the inflow state: kInflowTable doubles
+// followed by the same kInflowTable values rounded to binary32 (the FP32
+// adjoint kernels read the float copy, so their ghost cells convert nothing).
+constexpr int kInflowTable = 38 * 3;
 cudaError_t launch_inflow_derivs(const Phys& ph, double* out, cudaStream_t stream);
 cudaError_t launch_adjoint_fields(int prec, const Geom& g, const Phys& ph, const double* n0, const double* eps0,
                                   const double* beta0, const void* A0, const void* lam0, double* dn0,
