@@ -170,9 +170,13 @@ class _RLBRun(torch.autograd.Function):
         sim = RLB(spec.nx, spec.ny, spec.nz, float(tau), spec.c_l, spec.precision, spec.xbc, spec.n_in, spec.eps_in,
                   tuple(float(v) for v in beta_in.detach().cpu().tolist()), spec.n_ref, spec.eps_ref,
                   device=spec.device)
+        try:
+            plan = spec.plan(sim.state_bytes)
+        except ValueError:
+            sim.close()
+            raise
         n0c, e0c, b0c = (t.detach().to(spec.device, torch.float64).contiguous() for t in (n0, eps0, beta0))
         sim.init_fields(n0c, e0c, b0c, spec.solid)
-        plan = spec.plan(sim.state_bytes)
         checkpoints, tail = forward_states(sim, plan)
         n, e, b, ok = sim.macro()
         spec.last_sim, spec.last_plan = sim, plan
