@@ -614,20 +614,22 @@ def run_ours(args):
 
 
 def run_reference(args):
-    """The FP64 CPU oracle (the reference arm): each step is one oracle step of
-    a bounded sample of the workload (a 10-plane z slab of the sphere lattice)."""
+    """The FP64 CPU oracle (the reference arm) on the benchmark workload: each
+    step is one oracle step of a bounded sample of it (a 10-plane z slab
+    through the middle of the lattice: the sphere's centre plane for the
+    sphere)."""
     ws, rank, local = dist_env()
     if rank != 0:
         return
     import oracle
     import workloads as W
 
-    w = W.sphere_3d()
+    w, wdesc = make_workload(args.workload, args.steps)
     nz = 10
-    z0 = 45
-    sub = W.Workload("sphere_slab", w.nx, w.ny, nz, w.tau, w.c_l, w.xbc, args.steps, w.n[z0:z0 + nz].copy(),
-                     w.eps[z0:z0 + nz].copy(), w.beta[:, z0:z0 + nz].copy(), w.solid[z0:z0 + nz].copy(),
-                     w.n_in, w.eps_in, w.beta_in)
+    z0 = w.nz // 2 - nz // 2
+    sl = lambda a: None if a is None else np.ascontiguousarray(a[..., z0:z0 + nz, :, :])
+    sub = W.Workload(w.name + "_slab", w.nx, w.ny, nz, w.tau, w.c_l, w.xbc, args.steps, sl(w.n), sl(w.eps),
+                     sl(w.beta), sl(w.solid), w.n_in, w.eps_in, w.beta_in)
     p = oracle.Params(**sub.params())
     st = oracle.init(p, sub.n, sub.eps, sub.beta, sub.solid)
     oracle.run(p, st, args.warmup, solid=sub.solid)
@@ -635,11 +637,11 @@ def run_reference(args):
     oracle.run(p, st, args.steps, solid=sub.solid)
     dt = time.time() - t0
     v = sub.N * args.steps / dt / 1e6
-    sample = f"{args.steps} FP64 oracle steps of a 200x100x{nz} z-slab of the sphere lattice"
+    sample = f"{args.steps} FP64 oracle steps of a {w.nx}x{w.ny}x{nz} z slab (z = {z0}..{z0 + nz - 1}) of the lattice"
     line = {"metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": "sphere_3d 200x100x100 (z-slab sample), tau=0.8"},
+            "config": {"workload": wdesc, "cells": w.N, "sample_cells": sub.N},
             "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": oracle.get_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
