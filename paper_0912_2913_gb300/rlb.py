@@ -45,6 +45,10 @@ class RLB:
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
             self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+            if self.stream != torch.cuda.current_stream(self.device):
+                # the workspace is used on the context's stream: its memory is
+                # reused only after that stream's work when it is freed
+                self.ws.record_stream(self.stream)
             self.ctx = N.rlb_create(self.params, self.stream.cuda_stream, self.ws, self.ws_bytes)
 
     @staticmethod
@@ -218,6 +222,13 @@ class RLB:
             self.close()
         except Exception:
             pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
 
     # -- layout helpers (marshalling between the state layout and arrays) -----
     def state_to_cells(self, state: torch.Tensor) -> torch.Tensor:
