@@ -102,3 +102,26 @@ def test_runspec_plan_from_bytes():
     p = spec.plan(1000)
     assert p.states_held <= 40 and p.P > 0
     assert RunSpec(8, 4, 4, 100).plan(1000).P == 0
+
+
+def test_schedule_sweep():
+    """Every (T, budget, K) with T < 40: either the plan is refused because
+    the plain checkpointed run does not fit, or every adjoint step sees its
+    own state, the held states are those counted and within the budget, and
+    no smaller head fits."""
+    for T in range(0, 40):
+        for K in (None, 1, 2, 3, 7):
+            for max_states in [None] + list(range(2, T + 4)):
+                try:
+                    plan = CheckpointPlan(T, max_states, K)
+                except ValueError:
+                    assert max_states is not None
+                    assert all(CheckpointPlan(T, None, K).held(H) > max_states for H in range(T + 1))
+                    continue
+                seen, recomputed, held = _run(plan)
+                assert seen == list(range(T - 1, -1, -1)), (T, K, max_states)
+                assert recomputed == plan.recomputed_steps and held == plan.states_held
+                assert plan.H + plan.P == T
+                if max_states is not None:
+                    assert held <= max_states
+                    assert all(plan.held(H) > max_states for H in range(plan.H))
