@@ -13,7 +13,7 @@ import torch
 
 import oracle
 import workloads as W
-from tests._helpers import gpu_run, oracle_run, rel_errors, tiny_workload
+from tests._helpers import gpu_run, light_cone_cells, light_cone_oracle, oracle_run, rel_errors, tiny_workload
 
 pytestmark = pytest.mark.gpu
 
@@ -211,6 +211,34 @@ def test_random_box_512_fp32_against_fp64_subsample():
     scale = np.abs(a0[:2]).max()
     assert np.all(np.abs(a1 - a0) <= 1e-12 * scale), (a0, a1)
     assert np.all(np.abs(b1 - b0) <= 1e-5 * scale), (b0, b1)
+
+
+@pytest.mark.slow
+def test_random_box_512_against_the_oracle_on_light_cones():
+    """At full size, against the oracle itself: 12 steps of the 512^3 box on
+    the GPU (FP64 and FP32, contexts made as the benchmark makes them) and,
+    at 48 seeded cells (the eight corners among them), the oracle's values
+    computed on each cell's 25^3 neighbourhood alone, which equal the
+    whole-lattice oracle bit for bit (tests/test_light_cone.py)."""
+    from paper_0912_2913_gb300 import RLB
+
+    k = 12
+    w = W.random_box(L=512, steps=k)
+    cells = light_cone_cells(w, 48, seed=512)
+    ref = light_cone_oracle(w, k, cells)
+    zs, ys, xs = (torch.tensor(c, dtype=torch.long, device="cuda:0") for c in zip(*cells))
+    for prec in ("fp64", "fp32"):
+        sim = RLB.from_workload(w, prec, device="cuda:0").init_fields(w.n, w.eps, w.beta)
+        sim.step(k)
+        n, e, b, ok = sim.macro()
+        got = (n[zs, ys, xs].cpu().numpy(), e[zs, ys, xs].cpu().numpy(), b[:, zs, ys, xs].cpu().numpy())
+        st = sim.stats()
+        sim.close()
+        del sim, n, e, b
+        torch.cuda.empty_cache()
+        assert ok and st["n_unphysical"] == 0
+        en, ee, eb = rel_errors(got, ref)
+        assert max(en, ee, eb) <= TOL[prec], (prec, en, ee, eb)
 
 
 def test_tachyon_lattice_speed():
