@@ -503,6 +503,12 @@ def traffic_from_profiles(kernel: str, digest: str, workload: str):
     return None
 
 
+def kernel_frac(w, ms, bytes_per_update, peak):
+    """Fraction of the HBM peak of one kernel launch over the lattice that
+    moves bytes_per_update per cell in ms milliseconds."""
+    return bytes_per_update * w.N / (ms * 1e-3) / 1e9 / peak
+
+
 def _leg(w, ms_total, steps, bytes_per_update, peak, extra=None):
     ms = ms_total / steps
     gbs = bytes_per_update * w.N / (ms * 1e-3) / 1e9
@@ -552,6 +558,8 @@ def run_ours(args):
                 ms_all, ms_k, _ = time_adjoint(sim, ka, 3)
                 legs["fp32_adjoint"] = _leg(w, ms_all, ka, BYTES_ADJ["fp32"] + BYTES_FWD["fp32"], peak,
                                             {"adjoint_kernel_ms": ms_k / ka,
+                                             "adjoint_kernel_frac_hbm": kernel_frac(w, ms_k / ka, BYTES_ADJ["fp32"],
+                                                                                    peak),
                                              "ratio_to_forward": (ms_all / ka) / (ms / args.steps)})
             sim.close()
             del sim
@@ -570,6 +578,8 @@ def run_ours(args):
                 ms_all, ms_k, _ = time_adjoint(sim, ka, 3)
                 legs["fp64_adjoint"] = _leg(w, ms_all, ka, BYTES_ADJ["fp64"] + BYTES_FWD["fp64"], peak,
                                             {"adjoint_kernel_ms": ms_k / ka,
+                                             "adjoint_kernel_frac_hbm": kernel_frac(w, ms_k / ka, BYTES_ADJ["fp64"],
+                                                                                    peak),
                                              "ratio_to_forward": (ms_all / ka) / (ms64 / k64)})
             legs["fp64_gamma_law_forward"] = gamma_law_leg(w, k64, device, peak, ms64 / k64)
             legs["shock_tube_fp64"] = shock_tube_graph_leg(device)
