@@ -133,6 +133,28 @@ def _ptr(x) -> int | None:
     raise TypeError(f"cannot pass {type(x)} to librlb")
 
 
+def _dptr(x) -> int | None:
+    """Address of a device buffer: a CUDA tensor (a raw int address and None
+    pass through).  Host arrays and CPU tensors are refused here, before the
+    library could hand a host address to a kernel."""
+    if x is None or isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr") and getattr(x, "is_cuda", False):
+        return _ptr(x)
+    where = "a CPU tensor" if hasattr(x, "data_ptr") else type(x).__name__
+    raise ValueError(f"librlb expects a device buffer (a CUDA tensor) here, not {where}")
+
+
+def _wptr(x, where: int) -> int | None:
+    """Address of a buffer on the side that `where` names: RLB_DEVICE a CUDA
+    tensor, RLB_HOST a numpy array or a CPU tensor."""
+    if where == RLB_DEVICE:
+        return _dptr(x)
+    if hasattr(x, "data_ptr") and getattr(x, "is_cuda", False):
+        raise ValueError("librlb expects a host buffer here (RLB_HOST), not a CUDA tensor")
+    return _ptr(x)
+
+
 def _check(status: int, ctx=None, allow=()) -> int:
     if status == RLB_OK or status in allow:
         return status
@@ -168,7 +190,7 @@ def rlb_workspace_bytes(p: rlb_params) -> int:
 
 def rlb_create(p: rlb_params, stream: int, workspace, workspace_bytes: int) -> int:
     ctx = ctypes.c_void_p()
-    _check(load().rlb_create(ctypes.byref(p), stream, _ptr(workspace), workspace_bytes, ctypes.byref(ctx)))
+    _check(load().rlb_create(ctypes.byref(p), stream, _dptr(workspace), workspace_bytes, ctypes.byref(ctx)))
     return ctx.value
 
 
@@ -177,7 +199,8 @@ def rlb_destroy(ctx: int) -> None:
 
 
 def rlb_init_fields(ctx, n, eps, beta, solid, where) -> None:
-    _check(load().rlb_init_fields(ctx, _ptr(n), _ptr(eps), _ptr(beta), _ptr(solid), where), ctx)
+    _check(load().rlb_init_fields(ctx, _wptr(n, where), _wptr(eps, where), _wptr(beta, where), _wptr(solid, where),
+                                  where), ctx)
 
 
 def rlb_step(ctx, nsteps: int) -> None:
@@ -185,11 +208,11 @@ def rlb_step(ctx, nsteps: int) -> None:
 
 
 def rlb_step_into(ctx, src, dst) -> None:
-    _check(load().rlb_step_into(ctx, _ptr(src), _ptr(dst)), ctx)
+    _check(load().rlb_step_into(ctx, _dptr(src), _dptr(dst)), ctx)
 
 
 def rlb_step_into_counted(ctx, src, dst) -> None:
-    _check(load().rlb_step_into_counted(ctx, _ptr(src), _ptr(dst)), ctx)
+    _check(load().rlb_step_into_counted(ctx, _dptr(src), _dptr(dst)), ctx)
 
 
 def rlb_state_ptr(ctx) -> int:
@@ -199,16 +222,17 @@ def rlb_state_ptr(ctx) -> int:
 
 
 def rlb_save_state(ctx, dst) -> None:
-    _check(load().rlb_save_state(ctx, _ptr(dst)), ctx)
+    _check(load().rlb_save_state(ctx, _dptr(dst)), ctx)
 
 
 def rlb_load_state(ctx, src) -> None:
-    _check(load().rlb_load_state(ctx, _ptr(src)), ctx)
+    _check(load().rlb_load_state(ctx, _dptr(src)), ctx)
 
 
 def rlb_macro(ctx, state, n, eps, beta, where) -> int:
     """Returns RLB_OK or RLB_ERR_UNPHYSICAL (outputs written in both cases)."""
-    return _check(load().rlb_macro(ctx, _ptr(state), _ptr(n), _ptr(eps), _ptr(beta), where), ctx,
+    return _check(load().rlb_macro(ctx, _dptr(state), _wptr(n, where), _wptr(eps, where), _wptr(beta, where), where),
+                  ctx,
                   allow=(RLB_ERR_UNPHYSICAL,))
 
 
@@ -219,22 +243,23 @@ def rlb_stats(ctx) -> dict:
 
 
 def rlb_adjoint_macro(ctx, state, dL_dn, dL_deps, dL_dbeta, lam_out) -> None:
-    _check(load().rlb_adjoint_macro(ctx, _ptr(state), _ptr(dL_dn), _ptr(dL_deps), _ptr(dL_dbeta), _ptr(lam_out)), ctx)
+    _check(load().rlb_adjoint_macro(ctx, _dptr(state), _dptr(dL_dn), _dptr(dL_deps), _dptr(dL_dbeta), _dptr(lam_out)),
+           ctx)
 
 
 def rlb_adjoint_step(ctx, state_t, lam_in, lam_out, dL_dtau_accum, dL_dbeta_in_accum) -> None:
-    _check(load().rlb_adjoint_step(ctx, _ptr(state_t), _ptr(lam_in), _ptr(lam_out), _ptr(dL_dtau_accum),
-                                   _ptr(dL_dbeta_in_accum)), ctx)
+    _check(load().rlb_adjoint_step(ctx, _dptr(state_t), _dptr(lam_in), _dptr(lam_out), _dptr(dL_dtau_accum),
+                                   _dptr(dL_dbeta_in_accum)), ctx)
 
 
 def rlb_adjoint_step_noalloc(ctx, state_t, lam_in, lam_out, dL_dtau_accum, dL_dbeta_in_accum) -> None:
-    _check(load().rlb_adjoint_step_noalloc(ctx, _ptr(state_t), _ptr(lam_in), _ptr(lam_out), _ptr(dL_dtau_accum),
-                                           _ptr(dL_dbeta_in_accum)), ctx)
+    _check(load().rlb_adjoint_step_noalloc(ctx, _dptr(state_t), _dptr(lam_in), _dptr(lam_out), _dptr(dL_dtau_accum),
+                                           _dptr(dL_dbeta_in_accum)), ctx)
 
 
 def rlb_adjoint_fields(ctx, n0, eps0, beta0, lam0, dL_dn0, dL_deps0, dL_dbeta0, dL_dbeta_in_accum) -> None:
-    _check(load().rlb_adjoint_fields(ctx, _ptr(n0), _ptr(eps0), _ptr(beta0), _ptr(lam0), _ptr(dL_dn0), _ptr(dL_deps0),
-                                     _ptr(dL_dbeta0), _ptr(dL_dbeta_in_accum)), ctx)
+    _check(load().rlb_adjoint_fields(ctx, _dptr(n0), _dptr(eps0), _dptr(beta0), _dptr(lam0), _dptr(dL_dn0),
+                                     _dptr(dL_deps0), _dptr(dL_dbeta0), _dptr(dL_dbeta_in_accum)), ctx)
 
 
 def rlb_sync(ctx) -> None:
@@ -250,7 +275,7 @@ def rlb_last_error(ctx=None) -> str:
 
 
 def rlb_selftest_conversions(f_in, d_in, n, f2d_out, d2f_out) -> None:
-    _check(load().rlb_selftest_conversions(_ptr(f_in), _ptr(d_in), int(n), _ptr(f2d_out), _ptr(d2f_out)))
+    _check(load().rlb_selftest_conversions(_dptr(f_in), _dptr(d_in), int(n), _dptr(f2d_out), _dptr(d2f_out)))
 
 
 def rlb_debug_bounds_violations() -> int:

@@ -104,3 +104,29 @@ def test_release_library_refuses_the_bounds_debug_calls(native):
             call()
         assert ei.value.status == N.RLB_ERR_STATE
         assert "RLB_CHECK_BOUNDS" in N.rlb_last_error(None)
+
+
+def test_host_buffers_are_refused_where_device_buffers_are_expected(native):
+    """The binding refuses host memory (numpy arrays, CPU tensors) for the
+    device arguments, and CUDA tensors for host-side outputs, before any
+    library call: no kernel is ever handed a host address."""
+    import numpy as np
+    import torch
+
+    N = native
+    host_np = np.zeros(64)
+    host_t = torch.zeros(64, dtype=torch.float64)
+    for bad in (host_np, host_t):
+        with pytest.raises(ValueError, match="device buffer"):
+            N.rlb_step_into(None, bad, bad)
+        with pytest.raises(ValueError, match="device buffer"):
+            N.rlb_adjoint_step(None, bad, bad, bad, bad, bad)
+        with pytest.raises(ValueError, match="device buffer"):
+            N.rlb_macro(None, bad, None, None, None, N.RLB_HOST)
+        with pytest.raises(ValueError, match="device buffer"):
+            N.rlb_init_fields(None, bad, bad, bad, None, N.RLB_DEVICE)
+        with pytest.raises(ValueError, match="device buffer"):
+            N.rlb_create(N.make_params(8, 4, 4, 0.8), None, bad, 1 << 20)
+    assert N._dptr(None) is None and N._dptr(1234) == 1234
+    assert N._wptr(host_np, N.RLB_HOST) == host_np.ctypes.data
+    assert N._wptr(host_t, N.RLB_HOST) == host_t.data_ptr()
