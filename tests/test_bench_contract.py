@@ -56,3 +56,16 @@ def test_multi_rank_timing_takes_the_slowest_rank():
         assert ms_max == 15.0
         # whole-job throughput: both replicas' updates over the slowest time
         assert value == pytest.approx(2 * 1000 * 10 / 15e-3 / 1e6)
+
+
+def test_kernel_fraction_arithmetic():
+    """kernel_frac: bytes per cell x cells / launch time / peak (the adjoint
+    kernel of the sphere: 456 B x 2e6 cells in 0.2230 ms = 4.09 TB/s, 0.610 of
+    6701.5 GB/s)."""
+    import bench
+
+    class Lattice:
+        N = 2_000_000
+
+    assert abs(bench.kernel_frac(Lattice, 0.2230, 456, 6701.5) - 912e6 / 0.2230e-3 / 6701.5e9) < 1e-12
+    assert abs(bench.kernel_frac(Lattice, 0.2230, 456, 6701.5) - 0.6103) < 1e-4
