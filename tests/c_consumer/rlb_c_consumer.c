@@ -61,6 +61,24 @@ int main(void) {
     CHECK(rlb_create(&p, NULL, NULL, 0, &ctx) == RLB_ERR_ARG && ctx == NULL);
     CHECK(rlb_state_layout(NULL, &stride, &elem, &bytes) == RLB_ERR_ARG);
 
+    /* sizes at the limit N < 2^31 - 64 (all arithmetic in 64 bits) */
+    p.eos = RLB_EOS_ULTRA;
+    p.xbc = RLB_BC_PERIODIC;
+    p.prec = RLB_FP64;
+    p.nx = 2147483583; /* 2^31 - 65 */
+    p.ny = 1;
+    p.nz = 1;
+    CHECK(rlb_state_layout(&p, &stride, &elem, &bytes) == RLB_OK);
+    CHECK(stride == 2147483584LL && bytes == (size_t)38 * 2147483584ULL * 8u);
+    CHECK(rlb_workspace_bytes(&p, &ws) == RLB_OK && ws > 2 * bytes);
+    p.nx = 2147483584; /* 2^31 - 64 */
+    CHECK(rlb_state_layout(&p, &stride, &elem, &bytes) == RLB_ERR_ARG);
+    p.nx = 65536;
+    p.ny = 65536; /* N = 2^32: the product is formed in 64 bits */
+    CHECK(rlb_workspace_bytes(&p, &ws) == RLB_ERR_ARG);
+    p.nx = 0;
+    CHECK(rlb_create(&p, NULL, NULL, 0, &ctx) == RLB_ERR_ARG && ctx == NULL);
+
     CHECK(strcmp(rlb_status_str(RLB_OK), rlb_status_str(RLB_ERR_ARG)) != 0);
     CHECK(rlb_destroy(NULL) == RLB_OK);
     int64_t count = 0;
