@@ -397,3 +397,38 @@ def test_stored_tail_gives_the_same_gradient(prec):
     for other in out[1:]:
         for a, b in zip(out[0], other):
             assert torch.equal(torch.nan_to_num(a, nan=7.0), torch.nan_to_num(b, nan=7.0))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_runs_are_bitwise_reproducible(prec):
+    """Two identical runs on the reduced sphere (50 forward steps, then three
+    adjoint steps with their dL/dtau and dL/dbeta_in sums) give the same bits.
+    Every output element has one writer and every sum a fixed order, so a
+    run-to-run difference would reveal a race (compute-sanitizer's racecheck
+    is not available here)."""
+    from paper_0912_2913_gb300 import RLB
+
+    w = W.sphere_3d(nx=60, ny=30, nz=30)
+    runs = []
+    for _ in range(2):
+        sim = RLB.from_workload(w, prec, device="cuda:0").init_fields(w.n, w.eps, w.beta, w.solid)
+        sim.step(50)
+        n = sim.N
+        state = sim.state().clone()
+        g = torch.Generator(device="cpu").manual_seed(1)
+        lam = torch.zeros_like(state)
+        lam[:, :n] = torch.randn(38, n, generator=g, dtype=torch.float64).to(lam.dtype).cuda()
+        lo = torch.zeros_like(state)
+        acc = torch.zeros(4, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            sim.adjoint_step(state, lam, lo, acc[0:1], acc[1:4])
+            lam, lo = lo, lam
+        torch.cuda.synchronize()
+        ints = torch.int64 if prec == "fp64" else torch.int32
+        runs.append((state[:, :n].contiguous().view(ints).clone(), lam[:, :n].contiguous().view(ints).clone(),
+                     acc.view(torch.int64).clone(), sim.stats()))
+        sim.close()
+    (s0, l0, a0, st0), (s1, l1, a1, st1) = runs
+    assert torch.equal(s0, s1) and torch.equal(l0, l1) and torch.equal(a0, a1)
+    assert st0 == st1
+    assert a0.view(torch.float64)[0].item() != 0.0
