@@ -146,7 +146,8 @@ RLB_API rlb_status rlb_step_into(rlb_ctx* ctx, const void* src, void* dst);
  * next time step (steps, n_unphysical, first_bad, n_nonpositive_eq): a run
  * that keeps its states in caller buffers (the stored tail of a checkpointed
  * gradient run) reports the statistics of rlb_step.  The context's own state
- * is not touched.  Not in the paper.                                        */
+ * is not touched.  RLB_ERR_STATE before rlb_init_fields (the statistics start
+ * there), RLB_ERR_ARG for NULL or equal buffers.  Not in the paper.        */
 RLB_API rlb_status rlb_step_into_counted(rlb_ctx* ctx, const void* src, void* dst);
 
 /* Device pointer of the context's current state (valid until the next
