@@ -258,13 +258,22 @@ def test_shock_tube_gradient_vs_finite_differences():
     fdv = (_gpu_loss_and_grad(wp, T, target, "fp64", grad=False) -
            _gpu_loss_and_grad(wm, T, target, "fp64", grad=False)) / (2 * h)
     assert abs(np.sum(de * v) - fdv) <= 1e-5 * abs(fdv)
-    # FP32 gradient against the FP64 one.  This 2000-step tube runs through a
-    # strong shock (beta* = 0.54, outside the positivity bound); the FP32
-    # forward trajectory alone differs from FP64 at the 1e-5..1e-4 level and
-    # the tau gradient, a global sum, moves by ~4e-3 (measured): bound 1e-2.
+    # FP32 gradient against the FP64 one, with a bound derived from the
+    # conditioning of this loss.  The adjoint is seeded with
+    # dL/deps_T = 2 (eps_T - eps_tgt), a difference of two profiles that agree
+    # to a few per cent; the FP32 forward run is held to TOL32 = 1e-4 relative
+    # per cell, so its seed may carry a relative error up to
+    # TOL32 * r,  r = ||eps_T|| / ||eps_T - eps_tgt||  (about 38 here),
+    # and the gradient, linear in the seed, inherits it; the adjoint pass adds
+    # its own 1e-3 (the bound of the well-conditioned sphere gradient).
+    mask = _loss_mask(w)
+    miss = math.sqrt(L)
+    r = (np.linalg.norm(target[mask]) + miss) / miss
+    bound = 1e-4 * r + 1e-3
+    assert 20 < r < 60, r  # the conditioning this bound is written for
     L32, dtau32, _, de32, _, _ = _gpu_loss_and_grad(w, T, target, "fp32", K=45)
-    assert abs(dtau32 - dtau) <= 1e-2 * abs(dtau)
-    assert np.max(np.abs(de32 - de)) <= 1e-2 * np.max(np.abs(de))
+    assert abs(dtau32 - dtau) <= bound * abs(dtau), (dtau32, dtau, bound)
+    assert np.max(np.abs(de32 - de)) <= bound * np.max(np.abs(de)), bound
 
 
 def test_oracle_taped_gradient_shock_tube_short():

@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 from oracle import riemann
+from tests import _numpy_rlb as NR
 
 RNG = np.random.default_rng(20091215)
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -199,49 +200,13 @@ def _totals(orc, p, state, solid=None):
     return np.array([f.sum(), g.sum(), *(g @ (p.c_l * e)).sum(0)])
 
 
-# D3Q19 of the lattice description, in the velocity order of the build: rest,
-# +-x, +-y, +-z, then the twelve diagonals as opposite pairs.
-_E19 = np.array([(0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1),
-                 (1, 1, 0), (-1, -1, 0), (1, -1, 0), (-1, 1, 0), (1, 0, 1), (-1, 0, -1),
-                 (1, 0, -1), (-1, 0, 1), (0, 1, 1), (0, -1, -1), (0, 1, -1), (0, -1, 1)], float)
-_W19 = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
-
-
-def _brute_step_periodic(h, tau, c_l):
-    """One step of a periodic lattice written independently with numpy:
-    np.roll streaming (value at x - e_i moves to x), the moments, the
-    closed-form recovery, Eqs. equil1s/equil2as/equil2bs with u = beta, and
-    BGK relaxation.  h has shape (nz, ny, nx, 2, 19)."""
-    pulled = np.empty_like(h)
-    for i in range(19):
-        ex, ey, ez = (int(v) for v in _E19[i])
-        pulled[..., i] = np.roll(h[..., i], shift=(ez, ey, ex), axis=(0, 1, 2))
-    f, g = pulled[..., 0, :], pulled[..., 1, :]
-    S = f.sum(-1)
-    E = g.sum(-1)
-    Mv = c_l * g @ _E19
-    eps = -E + np.sqrt(4 * E ** 2 - 3 * (Mv ** 2).sum(-1))
-    beta = 3 * Mv / (3 * E + eps)[..., None]
-    b2 = (beta ** 2).sum(-1)
-    gam2 = 1 / (1 - b2)
-    n = S / np.sqrt(gam2)
-    cu = c_l * beta @ _E19.T  # c_i . u
-    feq = _W19 * (n * np.sqrt(gam2))[..., None] * (1 + 3 * cu / c_l ** 2)
-    eg = (eps * gam2)[..., None]
-    geq = _W19 * eg * (1 / (gam2[..., None] * c_l ** 2) + 4 * cu / c_l ** 2 + 6 * cu ** 2 / c_l ** 4
-                       - 2 * b2[..., None] / c_l ** 2)
-    geq[..., 0] = _W19[0] * eps * gam2 * (4 - (2 + c_l ** 2) / (gam2 * c_l ** 2) - 2 * b2 / c_l ** 2)
-    eq = np.stack([feq, geq], axis=-2)
-    return pulled - (pulled - eq) / tau
-
-
 @pytest.mark.parametrize("shape", [(1, 1, 1), (2, 3, 4), (3, 3, 3), (5, 2, 3)])
 @pytest.mark.parametrize("c_l", [1.0, 10.0])
 def test_brute_force_numpy_step(orc, shape, c_l):
     """Tiny periodic grids: five oracle steps against the numpy transcription
-    above (np.roll streaming), agreement to 1e-14 of the largest population."""
+    of tests/_numpy_rlb.py (np.roll streaming), agreement to 1e-14 of the largest population."""
     e, w, _ = orc.lattice()
-    assert np.array_equal(e, _E19) and np.allclose(w, _W19, rtol=0, atol=1e-17)
+    assert np.array_equal(e, NR.E19) and np.allclose(w, NR.W19, rtol=0, atol=1e-17)
     nx, ny, nz = shape
     rng = np.random.default_rng(nx * 100 + ny * 10 + nz)
     n0 = rng.uniform(0.5, 1.5, size=(nz, ny, nx))
@@ -253,7 +218,7 @@ def test_brute_force_numpy_step(orc, shape, c_l):
     b = a.copy()
     for t in range(5):
         a = orc.step(p, a, step_index=t)
-        b = _brute_step_periodic(b, 0.8, c_l)
+        b = NR.step(b, 0.8, c_l)
         for s in (0, 1):
             err = np.max(np.abs(a[..., s, :] - b[..., s, :])) / np.max(np.abs(b[..., s, :]))
             assert err <= 1e-14, (t, s, err)
