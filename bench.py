@@ -3,15 +3,22 @@
 Metric: MLUPS (million lattice-cell updates per second) and the fraction of
 the HBM roofline, FP32 vs FP64, forward and adjoint step, on one GB300.
 
-Workload (default): the 3D relativistic shock on a sphere, 200 x 100 x 100
-cells, inflow beta_x = 0.5, solid sphere r = 15, tau = 0.8, synthetic fields
-from ``workloads.sphere_3d``.  One bench step = one lattice time step (the
-fused stream-and-collide sweep over every cell) of the headline variant, FP32
-deviation storage; the state (608 MB for FP32 A+B) is larger than L2, so no
-flush is needed between steps.  Legs measured in the same run: FP64 forward,
-FP32 / FP64 adjoint step (forward recompute + adjoint kernel).
+Workload (default): the periodic 512^3 box (eps = 1 + 0.2 phi with phi a
+Gaussian random field filtered with sigma = 8 cells, n = eps^(3/4), a
+divergence-free beta with max |beta| = 0.3, tau = 0.7; ``workloads.random_box``).
+One bench step = one lattice time step (the fused stream-and-collide sweep
+over every cell) of the headline variant, FP32 deviation storage; a state
+(20.4 GB per FP32 buffer) is far larger than L2, so no flush is needed
+between steps.  Legs measured in the same run: FP64 forward, FP32 / FP64
+adjoint step (forward recompute + adjoint kernel), the general equation of
+state, the 3D shock on a sphere (200 x 100 x 100, forward, adjoint step and a
+whole 2000-step gradient), the launch-bound 1D shock tube, the accuracy of
+the FP32 path, an end-to-end job through host buffers and the oracle on the
+host cores.  MLUPS and bytes count the collided cells (not solid cells, not
+ghost planes).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload box512|sphere]
 
 Under torchrun (N > 1) every rank runs an independent replica of the
 workload (the lattice is not sharded: replicas only); value = all ranks'
@@ -37,12 +44,12 @@ if ROOT not in sys.path:
 METRIC = "MLUPS and % of HBM roofline, FP32 vs FP64, forward and adjoint step, 1 GB300"
 FALLBACK_HBM_GBS = 6800.0
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (vector and tensor), nominal
-# FP64 pipe work of one update of the all-FP64 step (57 moment additions,
-# ~28 recovery operations with IEEE sqrt and divisions counted at their
-# measured cost, ~125 equilibrium + BGK operations) and the measured DFMA rate
-# of the GB300 FP64 pipe (python -m paper_0912_2913_gb300.probes.run).
+# FP64 pipe instructions of one update of the all-FP64 step (57 moment
+# additions, ~28 recovery operations, ~125 equilibrium + BGK operations) and
+# the FP64 instruction rate derived from the nominal FP64 peak (1.25 TFLOP/s =
+# 625 G fused multiply-adds per second, one FP64 pipe instruction each).
 FP64_OPS_PER_UPDATE = 210
-FP64_MEASURED_GOPS = 529.0
+FP64_PEAK_GOPS = FP64_NOMINAL_TFLOPS * 1e3 / 2
 
 # Algorithmic bytes per lattice update (every population read once and written once).
 BYTES_FWD = {"fp64": 38 * 8 * 2, "fp32": 38 * 4 * 2}
@@ -201,7 +208,7 @@ def time_adjoint(sim, steps, warmup):
     the adjoint kernel, as the sqrt(T) checkpointed backward pass runs them."""
     import torch
 
-    s0 = sim.state().clone()
+    s0 = sim.state()  # read only below
     s1 = sim.new_state()
     l_in = torch.zeros_like(s0)
     l_out = torch.zeros_like(s0)
@@ -249,7 +256,7 @@ def cpu_baseline(w, budget_s=12.0):
         if time.time() - t0 > budget_s and k >= 2:
             break
     dt = time.time() - t0
-    out = {"value": w.N * k / dt / 1e6, "unit": "MLUPS", "cores": oracle.get_threads(), "kind": "oracle",
+    out = {"value": collided_cells(w) * k / dt / 1e6, "unit": "MLUPS", "cores": oracle.get_threads(), "kind": "oracle",
            "sample": f"{k} FP64 oracle steps of the full {w.nx}x{w.ny}x{w.nz} sphere lattice ({dt:.1f} s)"}
     out["detail"] = oracle_thread_scaling(w)
     return out
@@ -310,7 +317,7 @@ def oracle_thread_scaling(w, budget_s=2.0):
         for label, t in (("threads_1", 1), ("threads_all", nthr)):
             oracle.set_threads(t)
             st = oracle.init(p, wl.n, wl.eps, wl.beta, wl.solid)
-            v, k = _oracle_mlups(p, st, wl.solid, wl.N, budget_s, ms)
+            v, k = _oracle_mlups(p, st, wl.solid, collided_cells(wl), budget_s, ms)
             res.setdefault(name, {})[label] = {"mlups": v, "steps": k}
     oracle.set_threads(nthr)
     return res
@@ -345,7 +352,7 @@ def accuracy_leg(w, steps, device):
             "fp32_max_rel_err": {"n": en, "eps": ee, "beta": eb}, "unphysical": {"fp64": u0, "fp32": u1}}
 
 
-def gamma_law_leg(w, steps, device, peak, ms_eps3p):
+def gamma_law_leg(w, steps, device, peak, ms_eps3p, cells):
     """The FP64 step with the general equation of state (an ideal gas with
     rest mass, Gamma = 1.2, m = 0.3: Newton recovery) on the same workload."""
     import torch
@@ -358,7 +365,7 @@ def gamma_law_leg(w, steps, device, peak, ms_eps3p):
     st = sim.stats()
     sim.close()
     torch.cuda.empty_cache()
-    leg = _leg(w, ms, steps, BYTES_FWD["fp64"], peak,
+    leg = _leg(cells, ms, steps, BYTES_FWD["fp64"], peak,
                {"eos": "P = (Gamma - 1)(eps - n m), Gamma = 1.2, m = 0.3", "bound": "alu",
                 "ratio_to_eps3p_step": (ms / steps) / ms_eps3p, "n_unphysical": st["n_unphysical"]})
     return leg
@@ -400,7 +407,7 @@ def shock_tube_graph_leg(device, steps_per_graph=100, replays=20):
     sim.close()
     return {"workload": "shock tube 1600x1x1 FP64, outflow ghosts at both ends", "us_per_step_stream": us_plain,
             "us_per_step_graph": us_graph, "steps_per_graph": steps_per_graph,
-            "mlups_graph": w.N / us_graph}
+            "mlups_graph": collided_cells(w) / us_graph}
 
 
 def gradient_run_leg(w, T, device, ms_forward, budget_cap=200e9, reserve=40e9):
@@ -458,7 +465,7 @@ def gradient_run_leg(w, T, device, ms_forward, budget_cap=200e9, reserve=40e9):
     return out
 
 
-def e2e_run(w, job_steps, jobs, device):
+def e2e_run(w, job_steps, jobs, device, cells):
     """End to end through the public API: host fields -> rlb_init_fields
     (H2D) -> job_steps steps -> rlb_macro to host (D2H), FP32."""
     import torch
@@ -483,7 +490,7 @@ def e2e_run(w, job_steps, jobs, device):
     sim.close()
     bi = hn.nbytes + he.nbytes + hb.nbytes + (0 if hs is None else hs.nbytes)
     bo = out[0].nbytes + out[1].nbytes + out[2].nbytes
-    return {"value": w.N * job_steps * jobs / dt / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": bi / job_steps,
+    return {"value": cells * job_steps * jobs / dt / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": bi / job_steps,
             "d2h_bytes_per_step": bo / job_steps,
             "job": f"{jobs} x (host fields -> init -> {job_steps} FP32 steps -> macro to host)"}
 
@@ -503,31 +510,135 @@ def traffic_from_profiles(kernel: str, digest: str, workload: str):
     return None
 
 
-def kernel_frac(w, ms, bytes_per_update, peak):
+def collided_cells(w) -> int:
+    """Cells a step collides: every cell but the solid ones and the x ghost
+    planes of a non-periodic lattice."""
+    n = w.N
+    if w.solid is not None:
+        n -= int(np.count_nonzero(w.solid))
+    if w.xbc != 0:
+        ghost = np.ones((w.nz, w.ny, 2), bool)
+        if w.solid is not None:
+            ghost &= w.solid[:, :, [0, -1]] == 0
+        n -= int(ghost.sum())
+    return n
+
+
+def kernel_frac(w, ms, bytes_per_update, peak, cells=None):
     """Fraction of the HBM peak of one kernel launch over the lattice that
-    moves bytes_per_update per cell in ms milliseconds."""
-    return bytes_per_update * w.N / (ms * 1e-3) / 1e9 / peak
+    moves bytes_per_update per collided cell in ms milliseconds."""
+    cells = w.N if cells is None else cells
+    return bytes_per_update * cells / (ms * 1e-3) / 1e9 / peak
 
 
-def _leg(w, ms_total, steps, bytes_per_update, peak, extra=None):
+def _leg(cells, ms_total, steps, bytes_per_update, peak, extra=None):
     ms = ms_total / steps
-    gbs = bytes_per_update * w.N / (ms * 1e-3) / 1e9
-    d = {"mlups": w.N / (ms * 1e-3) / 1e6, "ms_per_step": ms, "bytes_per_update": bytes_per_update,
+    gbs = bytes_per_update * cells / (ms * 1e-3) / 1e9
+    d = {"mlups": cells / (ms * 1e-3) / 1e6, "ms_per_step": ms, "bytes_per_update": bytes_per_update,
          "achieved_gbs": gbs, "frac_hbm": gbs / peak}
     if extra:
         d.update(extra)
     return d
 
 
-def make_workload(name, steps):
+BOX_DESC = ("random_box 512^3 periodic, eps = 1 + 0.2 phi (Gaussian random field, sigma 8, max|phi| = 1), "
+            "n = eps^(3/4), div-free beta, max|beta| = 0.3, tau = 0.7")
+SPHERE_DESC = ("sphere_3d 200x100x100, inflow plane x = 0 at beta_x = 0.5, eps = n = 1; interior at rest with "
+               "n = 0.3 and eps = 1 (the literal eps = 0.1 leaves the scheme's domain within 30 steps); solid "
+               "sphere r = 15 at (60,50,50); outflow copy at x = 199; tau = 0.8")
+
+
+def make_workload(name):
+    """The named workload with its own step count (box 1000, sphere 5000)."""
     import workloads as W
 
     if name == "box512":
-        return W.random_box(L=512, steps=steps), ("random_box 512^3 periodic, eps = 1 + 0.2 phi (Gaussian random "
-                                                  "field, sigma 8), n = eps^(3/4), div-free beta, max|beta| = 0.3, "
-                                                  "tau = 0.7")
-    return W.sphere_3d(steps=steps), ("sphere_3d 200x100x100, inflow beta_x = 0.5, eps = n = 1; interior at rest, "
-                                      "eps = 1, n = 0.3; solid sphere r = 15 at (60,50,50); tau = 0.8")
+        return W.random_box(L=512), BOX_DESC
+    return W.sphere_3d(), SPHERE_DESC
+
+
+def time_noalloc(sim, steps):
+    """ms per call of rlb_adjoint_step_noalloc (the persistent register
+    kernel + finalize) on the context's state, after one set-up call."""
+    import torch
+
+    from paper_0912_2913_gb300 import _native as Nat
+
+    s0 = sim.state()
+    l_in = torch.zeros_like(s0)
+    l_out = torch.zeros_like(s0)
+    acc = torch.zeros(4, dtype=torch.float64, device=sim.device)
+    Nat.rlb_adjoint_step_noalloc(sim.ctx, s0, l_in, l_out, acc[0:1], acc[1:4])
+    torch.cuda.synchronize()
+    a, b = _events(torch, sim.stream)
+    a.record(sim.stream)
+    for _ in range(steps):
+        Nat.rlb_adjoint_step_noalloc(sim.ctx, s0, l_in, l_out, acc[0:1], acc[1:4])
+    b.record(sim.stream)
+    torch.cuda.synchronize()
+    del l_in, l_out
+    return a.elapsed_time(b) / steps
+
+
+def precision_legs(w, prec, steps, peak, device, ms_fwd=None, adjoint=True):
+    """Forward leg (unless ms_fwd is given) and adjoint-step leg of one
+    precision on workload w; the adjoint step = forward recompute + adjoint
+    kernel, as the sqrt(T) backward pass runs them."""
+    import torch
+
+    from paper_0912_2913_gb300 import RLB
+
+    cells = collided_cells(w)
+    legs = {}
+    sim = RLB.from_workload(w, prec, device=device).init_fields(w.n, w.eps, w.beta, w.solid)
+    if ms_fwd is None:
+        ms, _ = time_forward(sim, steps, 3, 1, device)
+        ms_fwd = ms / steps
+        extra = None
+        if prec == "fp64":
+            extra = {"bound": "alu", "fp64_ops_per_update": FP64_OPS_PER_UPDATE,
+                     "fp64_peak_gops": FP64_PEAK_GOPS, "fp64_peak": "nominal 1.25 TFLOP/s = 625 G FMA/s",
+                     "fp64_alu_frac": FP64_OPS_PER_UPDATE * cells / (ms_fwd * 1e-3) / (FP64_PEAK_GOPS * 1e9)}
+        legs[f"{prec}_forward"] = _leg(cells, ms, steps, BYTES_FWD[prec], peak, extra)
+    else:
+        sim.step(3)
+    if adjoint:
+        ka = max(1, steps // 2)
+        ms_all, ms_k, _ = time_adjoint(sim, ka, 3)
+        ms_na = time_noalloc(sim, ka)
+        legs[f"{prec}_adjoint"] = _leg(cells, ms_all, ka, BYTES_ADJ[prec] + BYTES_FWD[prec], peak,
+                                       {"adjoint_kernel_ms": ms_k / ka,
+                                        "adjoint_kernel_frac_hbm": kernel_frac(w, ms_k / ka, BYTES_ADJ[prec], peak,
+                                                                               cells),
+                                        "noalloc_adjoint_ms": ms_na,
+                                        "ratio_to_forward": (ms_all / ka) / ms_fwd})
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    return legs
+
+
+def sphere_legs(steps, grad_steps, peak, device, adjoint=True):
+    """The 3D shock on a sphere as a leg of the box benchmark: FP32 forward,
+    FP32 adjoint step and a whole FP32 gradient run."""
+    import torch
+
+    from paper_0912_2913_gb300 import RLB
+
+    w, desc = make_workload("sphere")
+    cells = collided_cells(w)
+    sim = RLB.from_workload(w, "fp32", device=device).init_fields(w.n, w.eps, w.beta, w.solid)
+    ms, _ = time_forward(sim, steps, 20, 1, device)
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    out = {"workload": desc, "cells": w.N, "collided_cells": cells,
+           "fp32_forward": _leg(cells, ms, steps, BYTES_FWD["fp32"], peak)}
+    if adjoint:
+        out.update(precision_legs(w, "fp32", max(1, steps // 2), peak, device, ms_fwd=ms / steps))
+        if grad_steps > 0:
+            out["fp32_gradient_run"] = gradient_run_leg(w, grad_steps, device, ms / steps)
+    return out
 
 
 def run_ours(args):
@@ -540,7 +651,8 @@ def run_ours(args):
     from paper_0912_2913_gb300 import RLB
     from paper_0912_2913_gb300 import build as B
 
-    w, wdesc = make_workload(args.workload, args.steps)
+    w, wdesc = make_workload(args.workload)
+    cells = collided_cells(w)
     peak, peak_kind = measured_peaks()
     legs = {}
     with ClockSampler(local) as clk:
@@ -548,49 +660,31 @@ def run_ours(args):
         sim = RLB.from_workload(w, "fp32", device=device).init_fields(w.n, w.eps, w.beta, w.solid)
         ms, launches = time_forward(sim, args.steps, args.warmup, ws, device)
         ms_max = max_over_ranks(ms, ws, device)
-        value = aggregate(w.N, args.steps, ms_max, ws)
+        value = aggregate(cells, args.steps, ms_max, ws)
         stats32 = sim.stats()
-        legs["fp32_forward"] = _leg(w, ms, args.steps, BYTES_FWD["fp32"], peak)
+        legs["fp32_forward"] = _leg(cells, ms, args.steps, BYTES_FWD["fp32"], peak)
         achieved = legs["fp32_forward"]["achieved_gbs"] * args.steps / max(launches, 1)
-        if not args.headline_only:
-            ka = max(1, args.steps // 4)
-            if not args.no_adjoint:
-                ms_all, ms_k, _ = time_adjoint(sim, ka, 3)
-                legs["fp32_adjoint"] = _leg(w, ms_all, ka, BYTES_ADJ["fp32"] + BYTES_FWD["fp32"], peak,
-                                            {"adjoint_kernel_ms": ms_k / ka,
-                                             "adjoint_kernel_frac_hbm": kernel_frac(w, ms_k / ka, BYTES_ADJ["fp32"],
-                                                                                    peak),
-                                             "ratio_to_forward": (ms_all / ka) / (ms / args.steps)})
-            sim.close()
-            del sim
-            torch.cuda.empty_cache()
-            if not args.no_adjoint and args.workload == "sphere" and args.grad_steps > 0:
-                legs["fp32_gradient_run"] = gradient_run_leg(w, args.grad_steps, device, ms / args.steps)
-            sim = RLB.from_workload(w, "fp64", device=device).init_fields(w.n, w.eps, w.beta, w.solid)
-            k64 = max(1, args.steps // 4)
-            ms64, _ = time_forward(sim, k64, max(3, args.warmup // 4), 1, device)
-            legs["fp64_forward"] = _leg(w, ms64, k64, BYTES_FWD["fp64"], peak,
-                                        {"bound": "alu", "fp64_ops_per_update": FP64_OPS_PER_UPDATE,
-                                         "fp64_alu_frac": FP64_OPS_PER_UPDATE * w.N / (ms64 / k64 * 1e-3) /
-                                         (FP64_MEASURED_GOPS * 1e9)})
-            if not args.no_adjoint:
-                ka = max(1, k64 // 2)
-                ms_all, ms_k, _ = time_adjoint(sim, ka, 3)
-                legs["fp64_adjoint"] = _leg(w, ms_all, ka, BYTES_ADJ["fp64"] + BYTES_FWD["fp64"], peak,
-                                            {"adjoint_kernel_ms": ms_k / ka,
-                                             "adjoint_kernel_frac_hbm": kernel_frac(w, ms_k / ka, BYTES_ADJ["fp64"],
-                                                                                    peak),
-                                             "ratio_to_forward": (ms_all / ka) / (ms64 / k64)})
-            legs["fp64_gamma_law_forward"] = gamma_law_leg(w, k64, device, peak, ms64 / k64)
-            legs["shock_tube_fp64"] = shock_tube_graph_leg(device)
         sim.close()
         del sim
         torch.cuda.empty_cache()
+        if not args.headline_only:
+            k_side = max(1, args.steps // (10 if args.workload == "box512" else 4))
+            if not args.no_adjoint:
+                legs.update(precision_legs(w, "fp32", k_side * 2, peak, device, ms_fwd=ms / args.steps))
+            legs.update(precision_legs(w, "fp64", k_side, peak, device, adjoint=not args.no_adjoint))
+            legs["fp64_gamma_law_forward"] = gamma_law_leg(w, k_side, device, peak,
+                                                           legs["fp64_forward"]["ms_per_step"], cells)
+            if args.workload == "sphere":
+                if not args.no_adjoint and args.grad_steps > 0:
+                    legs["fp32_gradient_run"] = gradient_run_leg(w, args.grad_steps, device, ms / args.steps)
+            else:
+                legs["sphere"] = sphere_legs(1000, args.grad_steps, peak, device, adjoint=not args.no_adjoint)
+            legs["shock_tube_fp64"] = shock_tube_graph_leg(device)
     clocks = clk.summary()
-    accuracy = accuracy_leg(w, min(args.steps, 1000), device) if (rank == 0 and not args.headline_only) else None
+    accuracy = accuracy_leg(w, min(w.steps, 1000), device) if (rank == 0 and not args.headline_only) else None
     e2e = None
     if rank == 0 and not args.no_e2e:
-        e2e = e2e_run(w, args.e2e_steps, 1, device)
+        e2e = e2e_run(w, args.e2e_steps or w.steps, 1, device, cells)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, args.cpu_budget) if args.workload == "sphere" else cpu_baseline_slab(w, 32)
@@ -601,13 +695,14 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wdesc + "; FP32 deviation storage, FP64 recovery root", "cells": w.N,
+                       "collided_cells": cells,
                        "l2": "state larger than L2 (no flush needed)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": traffic_from_profiles(kern, B.unit_digest("rlb_forward.cu"), args.workload),
                          "kernel": kern,
-                         "bytes_per_launch": BYTES_FWD["fp32"] * w.N},
+                         "bytes_per_launch": BYTES_FWD["fp32"] * cells},
             "legs": legs,
             "clocks": clocks,
             "e2e": e2e,
@@ -634,7 +729,7 @@ def run_reference(args):
     import oracle
     import workloads as W
 
-    w, wdesc = make_workload(args.workload, args.steps)
+    w, wdesc = make_workload(args.workload)
     nz = 10
     z0 = w.nz // 2 - nz // 2
     sl = lambda a: None if a is None else np.ascontiguousarray(a[..., z0:z0 + nz, :, :])
@@ -646,7 +741,7 @@ def run_reference(args):
     t0 = time.time()
     oracle.run(p, st, args.steps, solid=sub.solid)
     dt = time.time() - t0
-    v = sub.N * args.steps / dt / 1e6
+    v = collided_cells(sub) * args.steps / dt / 1e6
     sample = f"{args.steps} FP64 oracle steps of a {w.nx}x{w.ny}x{nz} z slab (z = {z0}..{z0 + nz - 1}) of the lattice"
     line = {"metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -687,7 +782,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=5000)
+    ap.add_argument("--e2e-steps", type=int, default=0,
+                    help="steps of the end-to-end job (0: the workload's own step count)")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -695,7 +791,7 @@ def main(argv=None):
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--grad-steps", type=int, default=2000,
                     help="steps of the whole-gradient leg (rlb_run forward + backward); 0 skips it")
-    ap.add_argument("--workload", choices=["sphere", "box512"], default="sphere")
+    ap.add_argument("--workload", choices=["box512", "sphere"], default="box512")
     ap.add_argument("--profile", choices=["step", "adjoint", "box"], default=None,
                     help="short run of one kernel family for ncu captures (no JSON bench line)")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")

@@ -36,6 +36,7 @@ from dataclasses import dataclass, field
 from typing import Optional
 
 import numpy as np
+import scipy.fft as _fft
 
 XBC_PERIODIC = 0
 XBC_INFLOW_OUTFLOW = 1
@@ -144,7 +145,7 @@ def _filtered_noise(shape, sigma: float, rng: np.random.Generator, ncomp: int):
     spectra = []
     for _ in range(ncomp):
         w = rng.standard_normal(shape)
-        spectra.append(np.fft.rfftn(w) * filt)
+        spectra.append(_fft.rfftn(w, workers=-1) * filt)
     return spectra, (kx, ky, kz)
 
 
@@ -152,7 +153,7 @@ def random_box(L: int = 512, tau: float = 0.7, steps: int = 1000, sigma: float =
                amp: float = 0.2, beta_max: float = 0.3, c_l: float = 1.0) -> Workload:
     shape = (L, L, L)
     (phi_hat,), _ = _filtered_noise(shape, sigma, np.random.default_rng(seeds[0]), 1)
-    phi = np.fft.irfftn(phi_hat, s=shape, axes=(0, 1, 2))
+    phi = _fft.irfftn(phi_hat, s=shape, axes=(0, 1, 2), workers=-1)
     del phi_hat
     phi = phi - phi.mean()
     phi /= np.abs(phi).max()
@@ -168,9 +169,9 @@ def random_box(L: int = 512, tau: float = 0.7, steps: int = 1000, sigma: float =
         A.append(a_hat)
     kx, ky, kz = k
     # beta = curl A, spectrally: (dAz/dy - dAy/dz, dAx/dz - dAz/dx, dAy/dx - dAx/dy)
-    beta[0] = np.fft.irfftn(1j * ky * A[2] - 1j * kz * A[1], s=shape, axes=(0, 1, 2))
-    beta[1] = np.fft.irfftn(1j * kz * A[0] - 1j * kx * A[2], s=shape, axes=(0, 1, 2))
-    beta[2] = np.fft.irfftn(1j * kx * A[1] - 1j * ky * A[0], s=shape, axes=(0, 1, 2))
+    beta[0] = _fft.irfftn(1j * ky * A[2] - 1j * kz * A[1], s=shape, axes=(0, 1, 2), workers=-1)
+    beta[1] = _fft.irfftn(1j * kz * A[0] - 1j * kx * A[2], s=shape, axes=(0, 1, 2), workers=-1)
+    beta[2] = _fft.irfftn(1j * kx * A[1] - 1j * ky * A[0], s=shape, axes=(0, 1, 2), workers=-1)
     del A
     bmag = np.sqrt((beta * beta).sum(0)).max()
     beta *= beta_max / bmag
