@@ -84,8 +84,17 @@ typedef enum { RLB_HOST = 0, RLB_DEVICE = 1 } rlb_where;
  * Newton iteration on P; FP64 states only, no discrete adjoint.            */
 typedef enum { RLB_EOS_ULTRA = 0, RLB_EOS_GAMMA_LAW = 1 } rlb_eos;
 
+/* z boundary (not in the paper: the decomposition of one lattice into z
+ * slabs).  RLB_ZBC_PERIODIC: the lattice is periodic in z.  RLB_ZBC_HALO: the
+ * context holds one z slab of a larger lattice, its planes z = 0 and
+ * z = nz-1 are ghost copies of the neighbouring slabs' edge planes, which the
+ * steps neither collide nor write, and rlb_halo_exchange refills them after
+ * every step; only z = 1 .. nz-2 are updated (nz >= 3).  The eps = 3P
+ * equation of state only; the adjoint entry points refuse such contexts.    */
+typedef enum { RLB_ZBC_PERIODIC = 0, RLB_ZBC_HALO = 1 } rlb_zbc;
+
 typedef struct {
-    int32_t nx, ny, nz;   /* lattice size; nx >= 3 unless periodic; N < 2^31           */
+    int32_t nx, ny, nz;   /* lattice size; nx >= 3 unless periodic; N <= 2^31 - 2^21   */
     int32_t prec;         /* rlb_precision                                              */
     int32_t xbc;          /* rlb_xbc                                                    */
     int32_t eos;          /* rlb_eos                                                    */
@@ -97,6 +106,8 @@ typedef struct {
                              f - f^eq(n_ref, eps_ref, beta = 0); must be > 0           */
     double eos_gamma;     /* RLB_EOS_GAMMA_LAW: adiabatic index, 1 < Gamma <= 2         */
     double eos_mass;      /* RLB_EOS_GAMMA_LAW: particle rest mass m >= 0               */
+    int32_t zbc;          /* rlb_zbc                                                    */
+    int32_t reserved;     /* must be 0                                                  */
 } rlb_params;
 
 /* Size of one state: plane stride in elements and element size in bytes;
@@ -201,20 +212,44 @@ RLB_API rlb_status rlb_adjoint_step(rlb_ctx* ctx, const void* state_t, const voi
  * memory at the point of the call -- code running under a caching allocator
  * or memory pool that owns all device memory, or a real-time loop that must
  * not synchronise (cudaMalloc/cudaFree can synchronise the device).
- * Same arguments, results and errors as rlb_adjoint_step, from the same
- * kernels launched as a persistent grid (SMs x 2 blocks for FP64, x 4 for
- * FP32, capped at N/128 blocks); the results agree with rlb_adjoint_step's
- * to rounding (the sums are grouped by another grid).  The
- * per-warp partial sums live in one static device array of 32768 doubles
- * (256 KiB) per device: a launch that would need more (16 doubles per
- * block) returns RLB_ERR_ARG and enqueues nothing; every launch writes all
- * the slots it reads, so nothing needs to start at zero.  The first call on
- * each device sets up the array's address (with that device current; make
- * the first call before any stream capture); the context's device must be
- * current.  Calls that overlap in time on one device (different streams or
- * contexts) share the array and race: serialise them.                     */
+ * Same arguments, results and errors as rlb_adjoint_step.  It always runs the
+ * persistent one-cell-per-thread register kernel of the adjoint (a grid of
+ * SMs x 2 blocks for FP64, x 4 for FP32, capped at N/128 blocks), not the
+ * staged FP32 kernel that rlb_adjoint_step uses by default, so its speed
+ * differs; its results agree with rlb_adjoint_step's to rounding (the sums
+ * are grouped by another grid).  The per-warp partial sums live in one static
+ * device array of 32768 doubles (256 KiB) per device: a launch that would
+ * need more (16 doubles per block) returns RLB_ERR_ARG and enqueues nothing;
+ * every launch writes all the slots it reads, so nothing needs to start at
+ * zero.  The first call on each device (and the first after the device's
+ * context was reset) does the set-up: it takes the array's address and loads
+ * every kernel this entry point launches, which may allocate and
+ * synchronise, so make that first call before any stream capture and before
+ * the code that must not allocate; later calls allocate nothing.  The
+ * context's device must be current.  Calls that overlap in time on one
+ * device (different streams or contexts) share the array and race:
+ * serialise them.                                                          */
 RLB_API rlb_status rlb_adjoint_step_noalloc(rlb_ctx* ctx, const void* state_t, const void* lam_in, void* lam_out,
                                             double* dL_dtau_accum, double* dL_dbeta_in_accum);
+
+/* Halo exchange between two z slabs of one lattice (the paper has no
+ * counterpart: this is the data movement of a z decomposition, one slab per
+ * context, on one device).  lower and upper: contexts with zbc =
+ * RLB_ZBC_HALO, the same nx, ny, precision and device; upper's slab lies
+ * directly above lower's (lower's last updated plane z = nz_l - 2 and upper's
+ * first updated plane z = 1 are neighbours in the whole lattice; for a
+ * lattice periodic in z, the last slab's upper neighbour is the first slab,
+ * and a single slab is its own neighbour: lower == upper).  In the current
+ * states of both contexts it copies the 10 populations with e_z = +1 (5 of
+ * f, 5 of g) of lower's plane z = nz_l - 2 into upper's ghost plane z = 0,
+ * and the 10 with e_z = -1 of upper's plane z = 1 into lower's ghost plane
+ * z = nz_l - 1: exactly what the next step pulls across the two faces.  One
+ * kernel launch on lower's stream; when upper's stream is another one, the
+ * copy is ordered after the work already enqueued there and before any work
+ * enqueued there later.  Call it after every step (rlb_step with nsteps = 1)
+ * of every slab and before the next step.  Errors: RLB_ERR_ARG for contexts
+ * that do not fit together, RLB_ERR_STATE before rlb_init_fields.          */
+RLB_API rlb_status rlb_halo_exchange(rlb_ctx* lower, rlb_ctx* upper);
 
 /* Gradient with respect to the initial fields of rlb_init_fields, given
  * lam0 = dL/dA_0 (device): writes dL/dn0, dL/deps0 (N) and dL/dbeta0 (3N),

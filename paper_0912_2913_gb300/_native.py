@@ -20,6 +20,7 @@ RLB_FP64, RLB_FP32_DEV = 0, 1
 RLB_BC_PERIODIC, RLB_BC_INFLOW_OUTFLOW, RLB_BC_OUTFLOW_BOTH = 0, 1, 2
 RLB_HOST, RLB_DEVICE = 0, 1
 RLB_EOS_ULTRA, RLB_EOS_GAMMA_LAW = 0, 1
+RLB_ZBC_PERIODIC, RLB_ZBC_HALO = 0, 1
 
 # Every symbol include/rlb.h declares.
 EXPORTS = (
@@ -27,7 +28,7 @@ EXPORTS = (
     "rlb_step_into", "rlb_step_into_counted", "rlb_state_ptr", "rlb_save_state", "rlb_load_state", "rlb_macro", "rlb_stats",
     "rlb_adjoint_macro", "rlb_adjoint_step", "rlb_adjoint_fields", "rlb_sync", "rlb_status_str", "rlb_last_error",
     "rlb_launch_count", "rlb_selftest_conversions", "rlb_adjoint_step_noalloc", "rlb_debug_bounds_violations",
-    "rlb_debug_bounds_selftest",
+    "rlb_debug_bounds_selftest", "rlb_halo_exchange",
 )
 
 
@@ -43,7 +44,8 @@ class rlb_params(ctypes.Structure):
                 ("tau", ctypes.c_double), ("c_l", ctypes.c_double),
                 ("n_in", ctypes.c_double), ("eps_in", ctypes.c_double), ("beta_in", ctypes.c_double * 3),
                 ("n_ref", ctypes.c_double), ("eps_ref", ctypes.c_double),
-                ("eos_gamma", ctypes.c_double), ("eos_mass", ctypes.c_double)]
+                ("eos_gamma", ctypes.c_double), ("eos_mass", ctypes.c_double),
+                ("zbc", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _lib = None
@@ -107,6 +109,7 @@ def load(build_if_missing: bool = True):
             "rlb_selftest_conversions": ([vp, vp, i64, vp, vp], st),
             "rlb_debug_bounds_violations": ([P(i64)], st),
             "rlb_debug_bounds_selftest": ([i64, i64, P(i64)], st),
+            "rlb_halo_exchange": ([vp, vp], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -165,8 +168,9 @@ def _check(status: int, ctx=None, allow=()) -> int:
 
 def make_params(nx, ny, nz, tau, c_l=1.0, prec=RLB_FP64, xbc=RLB_BC_PERIODIC, n_in=1.0, eps_in=1.0,
                 beta_in=(0.0, 0.0, 0.0), n_ref=1.0, eps_ref=1.0, eos=RLB_EOS_ULTRA, eos_gamma=4.0 / 3.0,
-                eos_mass=0.0) -> rlb_params:
+                eos_mass=0.0, zbc=RLB_ZBC_PERIODIC) -> rlb_params:
     p = rlb_params()
+    p.zbc, p.reserved = int(zbc), 0
     p.nx, p.ny, p.nz, p.prec, p.xbc, p.eos = int(nx), int(ny), int(nz), int(prec), int(xbc), int(eos)
     p.eos_gamma, p.eos_mass = float(eos_gamma), float(eos_mass)
     p.tau, p.c_l, p.n_in, p.eps_in = float(tau), float(c_l), float(n_in), float(eps_in)
@@ -294,3 +298,7 @@ def rlb_debug_bounds_selftest(index: int, n: int) -> int:
 
 def rlb_launch_count(ctx) -> int:
     return int(load().rlb_launch_count(ctx))
+
+
+def rlb_halo_exchange(lower, upper) -> None:
+    _check(load().rlb_halo_exchange(lower, upper), lower)

@@ -22,6 +22,7 @@
 // eq(n_in, eps_in, beta_in)), dL/dbeta_in = sum lambda_{t+1} d eq/d beta_in
 // are summed per warp (binary32 for the FP32 path, binary64 otherwise) and
 // then over the warp partials in a fixed order (k_finalize).
+#include <cuda.h>  // CUcontext type only; cuCtxGetCurrent is taken through the runtime
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -514,10 +515,12 @@ __global__ void __launch_bounds__(128, MINB)
     T tau_acc = 0;
     double bin0 = 0.0, bin1 = 0.0, bin2 = 0.0;
     bool has_b = false;
-    const int stride = PIPE ? gridDim.x * blockDim.x : g.N;
+    const long long stride = PIPE ? (long long)gridDim.x * blockDim.x : (long long)g.N;
     // the loop ends for every thread before the warp reduction ('continue'
-    // skips to the next cell)
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < g.N; idx += stride) {
+    // skips to the next cell); the counter is 64-bit so that the last
+    // stride cannot wrap
+    for (long long li = (long long)blockIdx.x * blockDim.x + threadIdx.x; li < g.N; li += stride) {
+        const int idx = (int)li;
         int x, y, z;
         cell_coords(g, idx, x, y, z);
         if ((XBC != XBC_PERIODIC) && (x == 0 || x == g.nx - 1)) {
@@ -634,7 +637,7 @@ __global__ void __launch_bounds__(kStageThreads, 3)
     extern __shared__ float stage[];  // [slot][value 0..37][thread]
     const I S = (I)g.S;
     const int tid = threadIdx.x;
-    const int stride = gridDim.x * blockDim.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
     const uint32_t scol = (uint32_t)__cvta_generic_to_shared(stage) + 4u * tid;
     auto sval = [&](int slot, int q) -> float { return stage[(slot * 38 + q) * kStageThreads + tid]; };
     auto is_ghost = [&](int x) { return XBC != XBC_PERIODIC && (x == 0 || x == g.nx - 1); };
@@ -652,26 +655,30 @@ __global__ void __launch_bounds__(kStageThreads, 3)
     float tau_acc = 0.0f;
     double bin0 = 0.0, bin1 = 0.0, bin2 = 0.0;
     bool has_b = false;
-    int idx = blockIdx.x * blockDim.x + tid;
+    // 64-bit loop counter: li + stride cannot wrap for any accepted N
+    long long li = (long long)blockIdx.x * blockDim.x + tid;
+    int idx = li < g.N ? (int)li : 0;
     int x = 0, y = 0, z = 0;
     PullOffsets o{};
-    if (idx < g.N) {
+    if (li < g.N) {
         cell_coords(g, idx, x, y, z);
         o = PullOffsets(g, x, y, z);
         if (!is_ghost(x)) issue(idx, o, 19, 0);
     }
     cp_async_commit();
     int sg = 0;
-    for (; idx < g.N; idx += stride) {
+    for (; li < g.N; li += stride) {
+        idx = (int)li;
         const int sf = sg == kStageSlots - 1 ? 0 : sg + 1;
         const int sn = sf == kStageSlots - 1 ? 0 : sf + 1;
         const bool ghost = is_ghost(x);
         if (!ghost) issue(idx, o, 0, sf);
         cp_async_commit();
-        const int nidx = idx + stride;
+        const long long nl = (long long)idx + stride;  // 64-bit: cannot wrap
+        const int nidx = nl < g.N ? (int)nl : 0;
         int xn = 0, yn = 0, zn = 0;
         PullOffsets on{};
-        if (nidx < g.N) {
+        if (nl < g.N) {
             cell_coords(g, nidx, xn, yn, zn);
             on = PullOffsets(g, xn, yn, zn);
         }
@@ -706,7 +713,7 @@ __global__ void __launch_bounds__(kStageThreads, 3)
                 cell_g(h, mug, c, r);
             }
         }
-        if (nidx < g.N && !is_ghost(xn)) issue(nidx, on, 19, sn);
+        if (nl < g.N && !is_ghost(xn)) issue(nidx, on, 19, sn);
         cp_async_commit();
         cp_async_wait<1>();  // F_k has landed
         // ---- f phase, scatter
@@ -1019,26 +1026,72 @@ static __device__ __align__(256) double g_adj_scratch[kAdjScratchDoubles];
 namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
-double* g_scratch_ptr[kMaxDevices];
-int g_scratch_nsm[kMaxDevices];
+struct ScratchSetup {
+    double* ptr;    // device address of g_adj_scratch in the context below
+    int nsm;        // SM count of the device
+    CUcontext ctx;  // the context the set-up was made in
+};
+ScratchSetup g_scratch[kMaxDevices];
 
-// Set-up once per device, with that device current: the device address of
-// g_adj_scratch and the SM count.
+// The calling thread's current context (the device's primary context under
+// the runtime API), through the driver entry point the runtime hands out, so
+// that the library needs no link against the driver library.
+CUcontext current_context() {
+    using Fn = CUresult (*)(CUcontext*);
+    static Fn fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<Fn>(f);
+        looked = true;
+    }
+    CUcontext c = nullptr;
+    if (fn) fn(&c);
+    return c;
+}
+
+// Set-up, with the device current: the device address of g_adj_scratch, the
+// SM count, and every kernel this entry point launches loaded onto the
+// device (cudaFuncGetAttributes loads a kernel that lazy module loading has
+// not loaded yet), so that no later call loads code, which can allocate.
+// Redone when the device's context is not the one it was made in (after
+// cudaDeviceReset the old address is stale).
 cudaError_t scratch_for_device(int dev, double** ptr, int* nsm) {
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    const CUcontext ctx = current_context();
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
+    ScratchSetup& s = g_scratch[dev];
+    if (!s.ptr || s.ctx != ctx) {
+        s.ptr = nullptr;
         double* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress((void**)&p, g_adj_scratch);
         if (e != cudaSuccess) return e;
         int n = 0;
         e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
-        g_scratch_nsm[dev] = n;
-        g_scratch_ptr[dev] = p;
+        const void* kernels[] = {
+            (const void*)k_adjoint_step<double, XBC_PERIODIC, 2, true>,
+            (const void*)k_adjoint_step<double, XBC_INFLOW_OUTFLOW, 2, true>,
+            (const void*)k_adjoint_step<double, XBC_OUTFLOW_BOTH, 2, true>,
+            (const void*)k_adjoint_step<float, XBC_PERIODIC, 4, true>,
+            (const void*)k_adjoint_step<float, XBC_INFLOW_OUTFLOW, 4, true>,
+            (const void*)k_adjoint_step<float, XBC_OUTFLOW_BOTH, 4, true>,
+            (const void*)k_finalize,
+        };
+        for (const void* k : kernels) {
+            cudaFuncAttributes attr;
+            e = cudaFuncGetAttributes(&attr, k);
+            if (e != cudaSuccess) return e;
+        }
+        s.nsm = n;
+        s.ctx = ctx;
+        s.ptr = p;
     }
-    *ptr = g_scratch_ptr[dev];
-    *nsm = g_scratch_nsm[dev];
+    *ptr = s.ptr;
+    *nsm = s.nsm;
     return cudaSuccess;
 }
 

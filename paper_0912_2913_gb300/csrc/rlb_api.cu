@@ -94,7 +94,11 @@ rlb_status check_params(const rlb_params* p) {
     if (!p) return fail(nullptr, RLB_ERR_ARG, "params is NULL");
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) return fail(nullptr, RLB_ERR_ARG, "lattice sizes must be >= 1");
     const long long N = (long long)p->nx * p->ny * p->nz;
-    if (N >= (1ll << 31) - 64) return fail(nullptr, RLB_ERR_ARG, "lattice too large (N must be < 2^31)");
+    // Cell indices are 32-bit in the kernels; the limit leaves 2^21 of room
+    // above the last cell for the thread indices of the last block and of a
+    // grid-stride step.
+    if (N > (1ll << 31) - (1ll << 21))
+        return fail(nullptr, RLB_ERR_ARG, "lattice too large (N must be <= 2^31 - 2^21)");
     if (p->prec != RLB_FP64 && p->prec != RLB_FP32_DEV) return fail(nullptr, RLB_ERR_ARG, "bad precision %d", p->prec);
     if (p->xbc < RLB_BC_PERIODIC || p->xbc > RLB_BC_OUTFLOW_BOTH) return fail(nullptr, RLB_ERR_ARG, "bad xbc %d", p->xbc);
     if (p->xbc != RLB_BC_PERIODIC && p->nx < 3) return fail(nullptr, RLB_ERR_ARG, "ghost planes need nx >= 3");
@@ -112,6 +116,12 @@ rlb_status check_params(const rlb_params* p) {
     }
     if (p->prec == RLB_FP32_DEV && (!(p->n_ref > 0) || !(p->eps_ref > 0)))
         return fail(nullptr, RLB_ERR_ARG, "FP32 deviation storage needs n_ref > 0 and eps_ref > 0");
+    if (p->zbc != RLB_ZBC_PERIODIC && p->zbc != RLB_ZBC_HALO) return fail(nullptr, RLB_ERR_ARG, "bad zbc %d", p->zbc);
+    if (p->reserved != 0) return fail(nullptr, RLB_ERR_ARG, "rlb_params.reserved must be 0");
+    if (p->zbc == RLB_ZBC_HALO) {
+        if (p->nz < 3) return fail(nullptr, RLB_ERR_ARG, "a z slab with halo planes needs nz >= 3");
+        if (p->eos != RLB_EOS_ULTRA) return fail(nullptr, RLB_ERR_ARG, "z slabs cover the eps = 3P equation of state");
+    }
     return RLB_OK;
 }
 
@@ -210,6 +220,7 @@ rlb_status rlb_create(const rlb_params* p, void* stream, void* workspace, size_t
     g.xbc = p->xbc;
     g.div_nx = make_fast_div((unsigned)g.nx);
     g.div_ny = make_fast_div((unsigned)g.ny);
+    g.zhalo = p->zbc == RLB_ZBC_HALO ? 1 : 0;
     {
         // Tuning knobs (no effect on results beyond rounding): RLB_TMA=1
         // selects the TMA-staged FP32 step, RLB_F32_VARIANT the launch variant
@@ -217,7 +228,7 @@ rlb_status rlb_create(const rlb_params* p, void* stream, void* workspace, size_t
         // per thread, 1: persistent, 2: persistent shared-memory staged;
         // RLB_ADJ_IDX64=1 its 64-bit offset variant on any lattice).
         const char* t = getenv("RLB_TMA");
-        g.tma = (t && t[0] == '1') ? 1 : 0;
+        g.tma = (t && t[0] == '1' && !g.zhalo) ? 1 : 0;  // the TMA-staged step updates every z plane
         const char* v = getenv("RLB_F32_VARIANT");
         g.variant = v ? atoi(v) : -1;  // -1: chosen by timing at the first step
         const char* ap = getenv("RLB_ADJ_PIPE");
@@ -532,6 +543,7 @@ rlb_status rlb_adjoint_macro(rlb_ctx* c, const void* state, const double* dL_dn,
                              const double* dL_dbeta, void* lam_out) {
     RLB_LATCHED(c);
     if (c->ph.eos) return fail(c, RLB_ERR_ARG, "the discrete adjoint covers the eps = 3P equation of state");
+    if (c->g.zhalo) return fail(c, RLB_ERR_ARG, "the discrete adjoint covers whole lattices (no z slabs)");
     if (!state || !dL_dn || !dL_deps || !dL_dbeta || !lam_out) return fail(c, RLB_ERR_ARG, "null pointer");
     return after_launch(c, launch_adjoint_macro(c->p.prec, c->g, c->ph, state, dL_dn, dL_deps, dL_dbeta, lam_out,
                                                 c->stream),
@@ -543,6 +555,7 @@ rlb_status rlb_adjoint_step(rlb_ctx* c, const void* state_t, const void* lam_in,
     Nvtx nvtx_("rlb_adjoint_step");
     RLB_LATCHED(c);
     if (c->ph.eos) return fail(c, RLB_ERR_ARG, "the discrete adjoint covers the eps = 3P equation of state");
+    if (c->g.zhalo) return fail(c, RLB_ERR_ARG, "the discrete adjoint covers whole lattices (no z slabs)");
     if (!state_t || !lam_in || !lam_out || lam_in == lam_out) return fail(c, RLB_ERR_ARG, "bad buffers");
     if (!dL_dtau_accum || !dL_dbeta_in_accum) return fail(c, RLB_ERR_ARG, "accumulators are required");
     return after_launch(c, launch_adjoint_step(c->p.prec, c->g, c->ph, state_t, lam_in, lam_out, c->red, c->inflow_d,
@@ -554,6 +567,7 @@ rlb_status rlb_adjoint_step_noalloc(rlb_ctx* c, const void* state_t, const void*
                                     double* dL_dtau_accum, double* dL_dbeta_in_accum) {
     RLB_LATCHED(c);
     if (c->ph.eos) return fail(c, RLB_ERR_ARG, "the discrete adjoint covers the eps = 3P equation of state");
+    if (c->g.zhalo) return fail(c, RLB_ERR_ARG, "the discrete adjoint covers whole lattices (no z slabs)");
     if (!state_t || !lam_in || !lam_out || lam_in == lam_out) return fail(c, RLB_ERR_ARG, "bad buffers");
     if (!dL_dtau_accum || !dL_dbeta_in_accum) return fail(c, RLB_ERR_ARG, "accumulators are required");
     int dev = -1;
@@ -576,12 +590,50 @@ rlb_status rlb_adjoint_fields(rlb_ctx* c, const double* n0, const double* eps0, 
                               double* dL_dn0, double* dL_deps0, double* dL_dbeta0, double* dL_dbeta_in_accum) {
     RLB_LATCHED(c);
     if (c->ph.eos) return fail(c, RLB_ERR_ARG, "the discrete adjoint covers the eps = 3P equation of state");
+    if (c->g.zhalo) return fail(c, RLB_ERR_ARG, "the discrete adjoint covers whole lattices (no z slabs)");
     if (!n0 || !eps0 || !beta0 || !lam0 || !dL_dn0 || !dL_deps0 || !dL_dbeta0 || !dL_dbeta_in_accum)
         return fail(c, RLB_ERR_ARG, "null pointer");
     if (!c->inited) return fail(c, RLB_ERR_STATE, "rlb_adjoint_fields needs the solid layout of rlb_init_fields");
     return after_launch(c, launch_adjoint_fields(c->p.prec, c->g, c->ph, n0, eps0, beta0, c->A, lam0, dL_dn0, dL_deps0,
                                                  dL_dbeta0, c->red, dL_dbeta_in_accum, c->stream),
                         "adjoint_fields");
+}
+
+rlb_status rlb_halo_exchange(rlb_ctx* lo, rlb_ctx* up) {
+    Nvtx nvtx_("rlb_halo_exchange");
+    RLB_LATCHED(lo);
+    RLB_LATCHED(up);
+    if (!lo->g.zhalo || !up->g.zhalo) return fail(lo, RLB_ERR_ARG, "rlb_halo_exchange needs contexts with zbc = RLB_ZBC_HALO");
+    if (lo->g.nx != up->g.nx || lo->g.ny != up->g.ny || lo->p.prec != up->p.prec || lo->p.xbc != up->p.xbc ||
+        lo->device != up->device)
+        return fail(lo, RLB_ERR_ARG, "slabs of one lattice need the same nx, ny, precision, x boundary and device");
+    if (!lo->inited || !up->inited) return fail(lo, RLB_ERR_STATE, "rlb_halo_exchange before rlb_init_fields");
+    int dev = -1;
+    RLB_CUDA(lo, cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev != lo->device) return fail(lo, RLB_ERR_STATE, "the slabs' device %d is not current (%d is)", lo->device, dev);
+    cudaEvent_t ev = nullptr;
+    const bool two = up->stream != lo->stream;
+    if (two) {
+        // lower's stream waits for upper's earlier work; upper's later work
+        // waits for the copy
+        RLB_CUDA(lo, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
+        cudaError_t e = cudaEventRecord(ev, up->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(lo->stream, ev, 0);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(ev);
+            return cuda_fail(lo, e, "halo exchange ordering");
+        }
+    }
+    rlb_status s = after_launch(lo, launch_halo_exchange(lo->elem, (long long)lo->g.nxy, lo->A, lo->g.S, lo->g.nz, up->A,
+                                                         up->g.S, lo->stream),
+                                "halo exchange");
+    if (two) {
+        cudaError_t e = cudaEventRecord(ev, lo->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(up->stream, ev, 0);
+        cudaEventDestroy(ev);
+        if (e != cudaSuccess && s == RLB_OK) s = cuda_fail(lo, e, "halo exchange ordering");
+    }
+    return s;
 }
 
 rlb_status rlb_selftest_conversions(const float* f_in, const double* d_in, int64_t n, double* f2d_out,

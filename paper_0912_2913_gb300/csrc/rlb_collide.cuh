@@ -16,6 +16,7 @@
 #pragma once
 
 #include "rlb_device.cuh"
+#include "rlb_dfloat.cuh"
 
 namespace rlb {
 
@@ -68,9 +69,10 @@ __device__ __forceinline__ void collide_cell_f32(Fetch fetch, Bounce bounce, Put
     const double Mx = f2d(mxf), My = f2d(myf), Mz = f2d(mzf);
     const double m2 = fma(Mx, Mx, fma(My, My, Mz * Mz));
     const double d4 = fma(E, E, -0.75 * m2);
-    const float y0 = rsqrtf(d2f_seed(d4));
-    const double s0 = d4 * f2d(y0);
-    const double sq = fma(fma(-s0, s0, d4), f2d(0.5f * y0), s0);
+    double y0, hy0;
+    rsqrt_seed(d4, y0, hy0);
+    const double s0 = d4 * y0;
+    const double sq = fma(fma(-s0, s0, d4), hy0, s0);
     const double eps = fma(2.0, sq, -E);
     const float Df = d2f(fma(3.0, E, eps));
     const float deps = d2f(eps - c.eps_ref);
@@ -114,6 +116,128 @@ __device__ __forceinline__ void collide_cell_f32(Fetch fetch, Bounce bounce, Put
     }
     unphys = !(pos_finite(sfull) && pos_finite(E) && nonneg_finite(d4) && pos_finite(eps) && below_one(b2));
     nonpos = nonpositive_eq(bx, by, bz, c.c_l);
+}
+
+// ---------------------------------------------------------------------------
+// Compensated FP32 deviation collision, used for lattice speeds c_l > 1.
+//
+// At c_l > 1 the velocity terms of the g equilibria (w_i eps gamma^2 4 q_i/c_l
+// in Eq. equil2as) are c_l times larger than their rest part, while the
+// moments that drive the flow -- the energy, the momentum and, multiplied by
+// c_l^2, the momentum flux -- are sums in which they cancel.  Storage in
+// binary32 keeps each population to a relative 2^-24, which the scheme
+// tolerates; binary32 arithmetic in the collision adds rounding errors of the
+// same size that are coherent across the 18 moving populations of a cell (one
+// rounded beta, one rounded eps gamma^2, weights and 1/c_l rounded to
+// binary32), so the collision no longer conserves energy and momentum to that
+// accuracy and the error grows over thousands of steps at low viscosity.
+// This variant keeps the binary32 storage and removes the arithmetic error:
+//   - the moment sums are compensated (error-free pair sums and differences,
+//     rounding errors of the running sums collected and added back);
+//   - the recovery and the equilibrium coefficients are formed in FP64 and
+//     carried as binary32 pairs;
+//   - the antisymmetric part of g^eq is formed from the momentum sums
+//     themselves, 3 w_p (e_p . M)/c_l, which equals w_p eps gamma^2 4 q_p/c_l
+//     for the recovered (eps, beta) (with eps = 3P, (4/3) eps gamma^2 beta =
+//     M), so the equilibrium carries exactly the momentum of the gathered
+//     populations;
+//   - every equilibrium value is a binary32 pair; the non-equilibrium part
+//     eq_i - h_i is rounded once to binary32 and the relaxed value
+//     h_i + omega (eq_i - h_i) once more, when it is stored.
+// ---------------------------------------------------------------------------
+template <bool SOLID, class Fetch, class Bounce, class Put>
+__device__ __forceinline__ void collide_cell_f32c(Fetch fetch, Bounce bounce, Put put, const Dev32& c, bool& unphys,
+                                                  bool& nonpos) {
+    const float om = c.omega;
+    // ---- phase 1: energy-momentum populations g_i ----
+    float gg[19];
+    gather_phase<SOLID>(gg, 19, fetch, bounce);
+    dfl dg[9];
+    CSum esum(gg[0]);
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        esum.add(two_sum(gg[2 * p + 1], gg[2 * p + 2]));
+        dg[p] = two_sum(gg[2 * p + 1], -gg[2 * p + 2]);
+    }
+    // M / c_l = sum_p (g_p - g_opp(p)) e_p, per component
+    CSum sx(dg[0].h), sy(dg[1].h), sz(dg[2].h);
+    sx.c = dg[0].l, sy.c = dg[1].l, sz.c = dg[2].l;
+    sx.add(dg[3]), sx.add(dg[4]), sx.add(dg[5]), sx.add(dg[6]);
+    sy.add(dg[3]), sy.add(df_neg(dg[4])), sy.add(dg[7]), sy.add(dg[8]);
+    sz.add(dg[5]), sz.add(df_neg(dg[6])), sz.add(dg[7]), sz.add(df_neg(dg[8]));
+    const dfl Dx = sx.result(), Dy = sy.result(), Dz = sz.result();
+    // Recovery in FP64: eps = 2 sqrt(E^2 - 3|M|^2/4) - E, beta = 3M/(3E + eps).
+    const double E = c.eps_ref + df_dbl(esum.result());
+    const double Mx = c.c_l_d * df_dbl(Dx), My = c.c_l_d * df_dbl(Dy), Mz = c.c_l_d * df_dbl(Dz);
+    const double m2 = fma(Mx, Mx, fma(My, My, Mz * Mz));
+    const double d4 = fma(E, E, -0.75 * m2);
+    double y0, hs;
+    rsqrt_seed(d4, y0, hs);
+    double sq = d4 * y0;
+    sq = fma(fma(-sq, sq, d4), hs, sq);
+    sq = fma(fma(-sq, sq, d4), hs, sq);
+    const double eps = fma(2.0, sq, -E);
+    const double D = fma(3.0, E, eps);
+    double rD = rcp_seed(D);
+    rD = fma(rD, fma(-D, rD, 1.0), rD);
+    rD = fma(rD, fma(-D, rD, 1.0), rD);
+    const double r3 = 3.0 * rD;
+    const double bx = Mx * r3, by = My * r3, bz = Mz * r3;
+    const double b2 = fma(bx, bx, fma(by, by, bz * bz));
+    const double omb2 = 1.0 - b2;
+    double gam2 = rcp_seed(omb2);
+    gam2 = fma(gam2, fma(-omb2, gam2, 1.0), gam2);
+    gam2 = fma(gam2, fma(-omb2, gam2, 1.0), gam2);
+    const double eg = eps * gam2;
+    const double deps = eps - c.eps_ref;
+    // g^eq_i - g^ref_i = w_i [k1 + k2 q_i^2] +- 3 w_i (e_i . M)/c_l,
+    //   k1 = (deps - 2 eg b2)/c_l^2, k2 = 6 eg / c_l^2 (per weight class)
+    const double k1 = (deps - 2.0 * eg * b2) * c.inv_cl2_d, k2 = 6.0 * eg * c.inv_cl2_d;
+    const dfl K1[2] = {df_of(k1 * (1.0 / 18.0)), df_of(k1 * (1.0 / 36.0))};
+    const dfl K2[2] = {df_of(k2 * (1.0 / 18.0)), df_of(k2 * (1.0 / 36.0))};
+    // 3 w_p as pairs: 1/6 and 1/12
+    const dfl A3[2] = {{(float)(1.0 / 6.0), (float)(1.0 / 6.0 - (double)(float)(1.0 / 6.0))},
+                       {(float)(1.0 / 12.0), (float)(1.0 / 12.0 - (double)(float)(1.0 / 12.0))}};
+    const dfl Bx = df_of(bx), By = df_of(by), Bz = df_of(bz);
+    const dfl qv[9] = {Bx, By, Bz, df_add(Bx, By), df_add(Bx, df_neg(By)), df_add(Bx, Bz), df_add(Bx, df_neg(Bz)),
+                       df_add(By, Bz), df_add(By, df_neg(Bz))};
+    const dfl ev[9] = {Dx, Dy, Dz, df_add(Dx, Dy), df_add(Dx, df_neg(Dy)), df_add(Dx, Dz), df_add(Dx, df_neg(Dz)),
+                       df_add(Dy, Dz), df_add(Dy, df_neg(Dz))};
+    {
+        // g_0^eq - g_0^ref = w_0 [deps (3 - 2/c_l^2) + eg b2 (4 - 2/c_l^2)]   (Eq. equil2bs)
+        const double g0 = (1.0 / 3.0) * fma(deps, 3.0 - 2.0 * c.inv_cl2_d, eg * b2 * (4.0 - 2.0 * c.inv_cl2_d));
+        put(19, __fmaf_rn(om, df_sub_round(df_of(g0), gg[0]), gg[0]));
+#pragma unroll
+        for (int p = 0; p < 9; ++p) {
+            const int cl = p < 3 ? 0 : 1;
+            const dfl gsym = df_add(df_mul(K2[cl], df_mul(qv[p], qv[p])), K1[cl]);
+            const dfl gasy = df_mul(A3[cl], ev[p]);
+            put(20 + 2 * p, __fmaf_rn(om, df_sub_round(df_add(gsym, gasy), gg[2 * p + 1]), gg[2 * p + 1]));
+            put(21 + 2 * p, __fmaf_rn(om, df_sub_round(df_add(gsym, df_neg(gasy)), gg[2 * p + 2]), gg[2 * p + 2]));
+        }
+    }
+    // ---- phase 2: number populations f_i ----
+    float f[19];
+    gather_phase<SOLID>(f, 0, fetch, bounce);
+    CSum ssum(f[0]);
+#pragma unroll
+    for (int i = 1; i < 19; ++i) ssum.add(f[i]);
+    const double dS = df_dbl(ssum.result());
+    const double S = c.n_ref_d + dS;
+    // f^eq_i - f^ref_i = w_i dS +- w_i 3 S q_i / c_l   (Eq. equil1s, n gamma = S)
+    const dfl FS[2] = {df_of(dS * (1.0 / 18.0)), df_of(dS * (1.0 / 36.0))};
+    const double fa = 3.0 * S * c.inv_cl_d;
+    const dfl FA[2] = {df_of(fa * (1.0 / 18.0)), df_of(fa * (1.0 / 36.0))};
+    put(0, __fmaf_rn(om, df_sub_round(df_of(dS * (1.0 / 3.0)), f[0]), f[0]));
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        const int cl = p < 3 ? 0 : 1;
+        const dfl fasy = df_mul(FA[cl], qv[p]);
+        put(2 * p + 1, __fmaf_rn(om, df_sub_round(df_add(FS[cl], fasy), f[2 * p + 1]), f[2 * p + 1]));
+        put(2 * p + 2, __fmaf_rn(om, df_sub_round(df_add(FS[cl], df_neg(fasy)), f[2 * p + 2]), f[2 * p + 2]));
+    }
+    unphys = !(pos_finite(S) && pos_finite(E) && nonneg_finite(d4) && pos_finite(eps) && below_one(b2));
+    nonpos = nonpositive_eq(d2f(bx), d2f(by), d2f(bz), c.c_l);
 }
 
 }  // namespace rlb

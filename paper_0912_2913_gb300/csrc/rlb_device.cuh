@@ -109,6 +109,36 @@ __device__ __forceinline__ float d2f_seed(double d) {
     return __uint_as_float(bits);
 }
 
+// Binary64 seeds of 1/sqrt(x) and 1/x for Newton iterations, taken from the
+// binary32 instructions for a positive normal binary64 x of any exponent:
+// x = m 2^k with m in [1, 4) (k even; for 1/sqrt) or in [1, 2) (for 1/x), the
+// binary32 seed is formed for m, and the result is multiplied by 2^(-k/2) or
+// 2^-k.  Both scalings are exact and are integer operations on the exponent
+// field, so no FP64 instruction is added.  Zero, subnormal, negative,
+// infinite and NaN arguments (states the callers flag as unphysical) take the
+// unscaled binary32 seed.
+__device__ __forceinline__ double scale_pow2(double x, int k) {  // x 2^k, x and the result normal
+    return __hiloint2double(__double2hiint(x) + k * (1 << 20), __double2loint(x));
+}
+__device__ __forceinline__ int seed_shift(double x, int emax) {
+    const int hi = __double2hiint(x);
+    const int e = (hi >> 20) & 0x7FF;
+    return (hi >= 0 && e >= 1 && e <= emax) ? e - 1023 : 0;
+}
+// y ~ 1/sqrt(x), and y/2
+__device__ __forceinline__ void rsqrt_seed(double x, double& y, double& half_y) {
+    const int k = seed_shift(x, 0x7FE) & ~1;
+    const float sf = rsqrtf(d2f_seed(scale_pow2(x, -k)));
+    const double s = f2d(sf), hs = f2d(0.5f * sf);
+    // k = 0 also for the special arguments, whose seed must not be rescaled
+    y = k == 0 ? s : scale_pow2(s, -(k / 2));
+    half_y = k == 0 ? hs : scale_pow2(s, -(k / 2) - 1);
+}
+__device__ __forceinline__ double rcp_seed(double x) {
+    const int k = seed_shift(x, 0x7FC);
+    return scale_pow2(f2d(__frcp_rn(d2f_seed(scale_pow2(x, -k)))), -k);
+}
+
 // Offsets (in cells) from cell (x, y, z) to the source x - e of a pull, for
 // the components -1 / 0 / +1 of e, with periodic wrap.  For a non-periodic x
 // the interior cells never wrap, so the same formula serves every case.

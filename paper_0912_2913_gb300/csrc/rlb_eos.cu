@@ -27,14 +27,16 @@ namespace rlb {
 namespace {
 
 __device__ __forceinline__ double rcp64(double a) {
-    double x = f2d(__frcp_rn(d2f_seed(a)));
+    double x = rcp_seed(a);
     x = fma(x, fma(-a, x, 1.0), x);
     x = fma(x, fma(-a, x, 1.0), x);
     return x;
 }
 
 __device__ __forceinline__ double rsqrt64(double a) {
-    double y = f2d(rsqrtf(d2f_seed(a)));
+    double y, half_y;
+    rsqrt_seed(a, y, half_y);
+    (void)half_y;
     y = y * fma(-0.5 * a * y, y, 1.5);
     y = y * fma(-0.5 * a * y, y, 1.5);
     return y;

@@ -36,6 +36,7 @@ __global__ void __launch_bounds__(128) k_step_f64(const double* __restrict__ A, 
     if (idx >= g.N) return;
     int x, y, z;
     cell_coords(g, idx, x, y, z);
+    if (g.zhalo && (z == 0 || z == g.nz - 1)) return;  // z halo planes: filled by the exchange
     const long long S = g.S;
     if (XBC != XBC_PERIODIC && (x == 0 || x == g.nx - 1)) {
         // Ghost planes are not collided.  The inflow plane keeps its fixed
@@ -77,25 +78,26 @@ __global__ void __launch_bounds__(128) k_step_f64(const double* __restrict__ A, 
     mz *= ph.c_l;
     // Recovery with eps = 3P: eps = -E + sqrt(4E^2 - 3M^2), beta = 3M/(3E + eps).
     // Square root and reciprocals from binary32 seeds (converted on the integer
-    // pipe) with two FP64 Newton corrections each: full double accuracy at a
-    // fraction of the IEEE sequences' cost on this GPU's FP64 pipe.
+    // pipe, valid for any exponent of the argument) with two FP64 Newton
+    // corrections each: full double accuracy at a fraction of the IEEE
+    // sequences' cost on this GPU's FP64 pipe.
     const double m2 = fma(mx, mx, fma(my, my, mz * mz));
     const double disc = fma(4.0 * E, E, -3.0 * m2);
-    const float ys = rsqrtf(d2f_seed(disc));
-    const double hs = f2d(0.5f * ys);
-    double sq = disc * f2d(ys);
+    double ys, hs;
+    rsqrt_seed(disc, ys, hs);
+    double sq = disc * ys;
     sq = fma(fma(-sq, sq, disc), hs, sq);
     sq = fma(fma(-sq, sq, disc), hs, sq);
     const double eps = sq - E;
     const double D = fma(3.0, E, eps);
-    double rD = f2d(__frcp_rn(d2f_seed(D)));
+    double rD = rcp_seed(D);
     rD = fma(rD, fma(-D, rD, 1.0), rD);
     rD = fma(rD, fma(-D, rD, 1.0), rD);
     const double r3 = 3.0 * rD;
     const double bx = mx * r3, by = my * r3, bz = mz * r3;
     const double b2 = fma(bx, bx, fma(by, by, bz * bz));
     const double omb2 = 1.0 - b2;
-    double gam2 = f2d(__frcp_rn(d2f_seed(omb2)));
+    double gam2 = rcp_seed(omb2);
     gam2 = fma(gam2, fma(-omb2, gam2, 1.0), gam2);
     gam2 = fma(gam2, fma(-omb2, gam2, 1.0), gam2);
     const bool unphys = !(pos_finite(sf) && pos_finite(E) && nonneg_finite(disc) && pos_finite(eps) && below_one(b2));
@@ -177,13 +179,15 @@ __global__ void __launch_bounds__(128) k_step_f64(const double* __restrict__ A, 
 // I: type of the element offsets, int when 38 S < 2^31 (fewer address
 // instructions: measured +2 % / +6 % for the two shapes the first step picks
 // from on the 200x100x100 sphere), else long long.
-template <int XBC, bool SOLID, int MINB, bool PREF, typename I = long long>
+// COMP: the compensated collision (collide_cell_f32c), run for c_l > 1.
+template <int XBC, bool SOLID, int MINB, bool PREF, typename I = long long, bool COMP = false>
 __global__ void __launch_bounds__(256, MINB) k_step_f32(const float* __restrict__ A, float* __restrict__ B, Geom g,
                                                         Dev32 c, Counters cnt, int count, long long step_index) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= g.N) return;
     int x, y, z;
     cell_coords(g, idx, x, y, z);
+    if (g.zhalo && (z == 0 || z == g.nz - 1)) return;  // z halo planes: filled by the exchange
     const I S = (I)g.S;
     if (XBC != XBC_PERIODIC && (x == 0 || x == g.nx - 1)) {
         if (XBC == XBC_INFLOW_OUTFLOW && x == 0) {
@@ -212,7 +216,10 @@ __global__ void __launch_bounds__(256, MINB) k_step_f32(const float* __restrict_
     auto fetch = [&](int q, int i) { return __ldg(RLB_CHK_PTR(A, q * S + idx + o.src(i), 38ll * S)); };
     auto bounce = [&](int q, int i) { return __ldg(RLB_CHK_PTR(A, (q - i + opp(i)) * S + idx, 38ll * S)); };  // link bounce-back
     bool unphys, nonpos;
-    collide_cell_f32<SOLID>(fetch, bounce, put, c, unphys, nonpos);
+    if (COMP)
+        collide_cell_f32c<SOLID>(fetch, bounce, put, c, unphys, nonpos);
+    else
+        collide_cell_f32<SOLID>(fetch, bounce, put, c, unphys, nonpos);
     if (count) count_flags(cnt, unphys, nonpos, (unsigned long long)step_index * (unsigned long long)g.N + idx);
 }
 
@@ -225,11 +232,12 @@ template <int XBC, bool SOLID, bool CS>
 __global__ void __launch_bounds__(256, 3) k_step_f32_pipe(const float* __restrict__ A, float* __restrict__ B, Geom g,
                                                           Dev32 c, Counters cnt, int count, long long step_index) {
     const long long S = g.S;
-    const int stride = gridDim.x * blockDim.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
     auto prefetch_cell = [&](int idx) {
         int x, y, z;
         cell_coords(g, idx, x, y, z);
         if (XBC != XBC_PERIODIC && (x == 0 || x == g.nx - 1)) return;
+        if (g.zhalo && (z == 0 || z == g.nz - 1)) return;
         const PullOffsets o(g, x, y, z);
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
@@ -237,12 +245,15 @@ __global__ void __launch_bounds__(256, 3) k_step_f32_pipe(const float* __restric
             asm volatile("prefetch.global.L2 [%0];" ::"l"(RLB_CHK_PTR(A, i * S + idx + o.src(i), 38ll * S)));
         }
     };
-    int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx < g.N) prefetch_cell(idx);
-    for (; idx < g.N; idx += stride) {
-        if (idx + stride < g.N) prefetch_cell(idx + stride);
+    // 64-bit loop counter: li + stride cannot wrap for any accepted N
+    long long li = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (li < g.N) prefetch_cell((int)li);
+    for (; li < g.N; li += stride) {
+        const int idx = (int)li;
+        if (li + stride < g.N) prefetch_cell((int)(li + stride));
         int x, y, z;
         cell_coords(g, idx, x, y, z);
+        if (g.zhalo && (z == 0 || z == g.nz - 1)) continue;
         if (XBC != XBC_PERIODIC && (x == 0 || x == g.nx - 1)) {
             if (XBC == XBC_INFLOW_OUTFLOW && x == 0) {
 #pragma unroll
@@ -420,6 +431,50 @@ __global__ void k_check_solid_planes(Geom g, const uint8_t* __restrict__ solid, 
 }
 
 // ---------------------------------------------------------------------------
+// Halo exchange of a z decomposition.  Plane q of a state is [z][y][x], so
+// the values of one population on one z plane are nxy consecutive elements.
+// blockIdx.y = 0..19: segments 0..9 carry the ten populations with e_z = +1
+// (f then g) from lower's plane nz_l - 2 to upper's plane 0; segments 10..19
+// the ten with e_z = -1 from upper's plane 1 to lower's plane nz_l - 1.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int zface_velocity(int j, int sign) {  // j-th velocity (0..4) with e_z = sign
+    int k = 0;
+    for (int i = 1; i < 19; ++i)
+        if (vel_z(i) == sign) {
+            if (k == j) return i;
+            ++k;
+        }
+    return -1;
+}
+
+template <typename T>
+__global__ void k_halo_exchange(long long nxy, T* __restrict__ lower, long long S_l, int nz_l, T* __restrict__ upper,
+                                long long S_u) {
+    const int seg = blockIdx.y;
+    const bool up = seg < 10;
+    const int j = up ? seg : seg - 10;
+    const int i = zface_velocity(j % 5, up ? 1 : -1);
+    const int q = (j < 5 ? 0 : 19) + i;
+    const T* src = up ? lower + q * S_l + (long long)(nz_l - 2) * nxy : upper + q * S_u + nxy;
+    T* dst = up ? upper + q * S_u : lower + q * S_l + (long long)(nz_l - 1) * nxy;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nxy; k += (long long)gridDim.x * blockDim.x)
+        dst[k] = src[k];
+}
+
+cudaError_t launch_halo_exchange(int elem, long long nxy, void* lower, long long S_lower, int nz_lower, void* upper,
+                                 long long S_upper, cudaStream_t st) {
+    g_last_launches = 1;
+    long long nb = (nxy + 255) / 256;
+    if (nb > 4096) nb = 4096;
+    const dim3 grid((unsigned)nb, 20);
+    if (elem == 8)
+        k_halo_exchange<double><<<grid, 256, 0, st>>>(nxy, (double*)lower, S_lower, nz_lower, (double*)upper, S_upper);
+    else
+        k_halo_exchange<float><<<grid, 256, 0, st>>>(nxy, (float*)lower, S_lower, nz_lower, (float*)upper, S_upper);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
 static inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
@@ -435,6 +490,10 @@ Dev32 make_dev32(const Phys& ph) {
     c.g0a = (float)(3.0 - 2.0 * ph.inv_cl2);
     c.g0b = (float)(4.0 - 2.0 * ph.inv_cl2);
     c.eps_ref = ph.eps_ref;
+    c.n_ref_d = ph.n_ref;
+    c.c_l_d = ph.c_l;
+    c.inv_cl_d = ph.inv_cl;
+    c.inv_cl2_d = ph.inv_cl2;
     return c;
 }
 
@@ -473,13 +532,24 @@ static void launch_step_t(int prec, const Geom& g, const Phys& ph, const void* A
                                                                     count ? 1 : 0, step_index);
     } else {
         const Dev32 c = make_dev32(ph);
-        if (g.tma && launch_step_f32_tma(g, c, (const float*)A, (float*)B, cnt, count, step_index, st) == cudaSuccess)
-            return;
-        cudaGetLastError();
         const int tb = step_block(g.N, 256);
         const unsigned nb = blocks_for(g.N, tb);
         const int cs = count ? 1 : 0;
         const bool idx32 = 38 * g.S < (1ll << 31);
+        if (ph.c_l > 1.0) {
+            // lattice speeds above 1: the compensated collision (one launch
+            // shape; the TMA-staged and tuning variants use the binary32 one)
+            if (idx32)
+                k_step_f32<XBC, SOLID, 2, false, int, true><<<nb, tb, 0, st>>>((const float*)A, (float*)B, g, c, cnt, cs,
+                                                                                 step_index);
+            else
+                k_step_f32<XBC, SOLID, 2, false, long long, true><<<nb, tb, 0, st>>>((const float*)A, (float*)B, g, c,
+                                                                                       cnt, cs, step_index);
+            return;
+        }
+        if (g.tma && launch_step_f32_tma(g, c, (const float*)A, (float*)B, cnt, count, step_index, st) == cudaSuccess)
+            return;
+        cudaGetLastError();
         switch (g.variant) {
             case 0: k_step_f32<XBC, SOLID, 3, false><<<nb, tb, 0, st>>>((const float*)A, (float*)B, g, c, cnt, cs, step_index); break;
             case 1:

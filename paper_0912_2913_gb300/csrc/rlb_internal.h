@@ -40,6 +40,7 @@ struct Geom {
     FastDiv div_nx, div_ny;
     int adj_pipe;  // FP32 adjoint kernel: 0 one cell per thread, 1 persistent, 2 staged (tuning)
     int adj_idx64;  // 1: 64-bit element offsets in the staged adjoint even where 32 bits suffice (testing)
+    int zhalo;      // 1: planes z = 0 and z = nz-1 are halo copies, not updated by a step
 };
 
 // Physical parameters, with the derived constants the kernels use.
@@ -57,6 +58,7 @@ struct Dev32 {
     float omega, omw, c_l, inv_cl, inv_cl2, n_ref;
     float g0a, g0b;  // 3 - 2/c_l^2 and 4 - 2/c_l^2
     double eps_ref;
+    double n_ref_d, c_l_d, inv_cl_d, inv_cl2_d;  // binary64 copies (compensated collision)
 };
 
 // Device-side statistics of a run (see rlb_stats).
@@ -84,6 +86,13 @@ cudaError_t launch_conversions(const float* fi, const double* di, long long n, d
 
 cudaError_t launch_check_solid_planes(const Geom& g, const uint8_t* solid, unsigned long long* flag,
                                       cudaStream_t stream);
+
+// Halo exchange between the current states of two z slabs (elem: 4 or 8
+// bytes): the e_z = +1 populations of lower's plane z = nz_l - 2 into upper's
+// plane 0, the e_z = -1 populations of upper's plane 1 into lower's plane
+// nz_l - 1.
+cudaError_t launch_halo_exchange(int elem, long long nxy, void* lower, long long S_lower, int nz_lower, void* upper,
+                                 long long S_upper, cudaStream_t stream);
 
 // Adjoint.  'red' holds 4 doubles of partial sums per 32-cell warp.
 inline long long adj_red_doubles(long long N) { return 4 * 4 * ((N + 127) / 128); }

@@ -16,6 +16,7 @@ _PREC = {"fp64": N.RLB_FP64, "fp32": N.RLB_FP32_DEV, "fp32dev": N.RLB_FP32_DEV}
 _EOS = {"ultra": N.RLB_EOS_ULTRA, "gamma_law": N.RLB_EOS_GAMMA_LAW}
 _XBC = {"periodic": N.RLB_BC_PERIODIC, "inflow_outflow": N.RLB_BC_INFLOW_OUTFLOW,
         "outflow_both": N.RLB_BC_OUTFLOW_BOTH}
+_ZBC = {"periodic": N.RLB_ZBC_PERIODIC, "halo": N.RLB_ZBC_HALO}
 
 
 def _require_cuda(device):
@@ -29,13 +30,14 @@ class RLB:
 
     def __init__(self, nx, ny, nz, tau, c_l=1.0, precision="fp64", xbc="periodic", n_in=1.0, eps_in=1.0,
                  beta_in=(0.0, 0.0, 0.0), n_ref=1.0, eps_ref=1.0, device=None, stream=None, eos="ultra",
-                 eos_gamma=4.0 / 3.0, eos_mass=0.0):
+                 eos_gamma=4.0 / 3.0, eos_mass=0.0, zbc="periodic"):
         self.device = _require_cuda(device)
         prec = _PREC[precision] if isinstance(precision, str) else int(precision)
         x = _XBC[xbc] if isinstance(xbc, str) else int(xbc)
         e = _EOS[eos] if isinstance(eos, str) else int(eos)
+        z = _ZBC[zbc] if isinstance(zbc, str) else int(zbc)
         self.params = N.make_params(nx, ny, nz, tau, c_l, prec, x, n_in, eps_in, beta_in, n_ref, eps_ref, e,
-                                    eos_gamma, eos_mass)
+                                    eos_gamma, eos_mass, z)
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.N = self.nx * self.ny * self.nz
         self.precision = "fp64" if prec == N.RLB_FP64 else "fp32"

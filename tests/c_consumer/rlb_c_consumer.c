@@ -61,17 +61,17 @@ int main(void) {
     CHECK(rlb_create(&p, NULL, NULL, 0, &ctx) == RLB_ERR_ARG && ctx == NULL);
     CHECK(rlb_state_layout(NULL, &stride, &elem, &bytes) == RLB_ERR_ARG);
 
-    /* sizes at the limit N < 2^31 - 64 (all arithmetic in 64 bits) */
+    /* sizes at the limit N <= 2^31 - 2^21 (all arithmetic in 64 bits) */
     p.eos = RLB_EOS_ULTRA;
     p.xbc = RLB_BC_PERIODIC;
     p.prec = RLB_FP64;
-    p.nx = 2147483583; /* 2^31 - 65 */
+    p.nx = 2145386496; /* 2^31 - 2^21 */
     p.ny = 1;
     p.nz = 1;
     CHECK(rlb_state_layout(&p, &stride, &elem, &bytes) == RLB_OK);
-    CHECK(stride == 2147483584LL && bytes == (size_t)38 * 2147483584ULL * 8u);
+    CHECK(stride == 2145386496LL && bytes == (size_t)38 * 2145386496ULL * 8u);
     CHECK(rlb_workspace_bytes(&p, &ws) == RLB_OK && ws > 2 * bytes);
-    p.nx = 2147483584; /* 2^31 - 64 */
+    p.nx = 2145386497; /* 2^31 - 2^21 + 1 */
     CHECK(rlb_state_layout(&p, &stride, &elem, &bytes) == RLB_ERR_ARG);
     p.nx = 65536;
     p.ny = 65536; /* N = 2^32: the product is formed in 64 bits */

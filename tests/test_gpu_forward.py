@@ -419,3 +419,28 @@ def test_unphysical_cells_are_counted_not_fatal():
     oracle.run(p, ref, 1, stats=os_)
     assert s["n_unphysical"] == os_.n_unphysical and s["first_bad"] == os_.first_bad
     sim.close()
+
+
+@pytest.mark.parametrize("scale", [1e-30, 1e30])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_fields_scaled_far_outside_binary32_squares(scale, prec):
+    """The scheme is homogeneous of degree one in (f, g): scaling n and eps by
+    s scales every population, n and eps by s and leaves beta unchanged.  At
+    s = 1e-30 and 1e+30 the recovery's discriminant (~ s^2) lies far outside
+    the binary32 range that the FP64 path's Newton seeds come from; the shock
+    tube, 300 steps, still matches the oracle on the same scaled inputs (FP64
+    1e-10, FP32 1e-4) and the unscaled GPU run divided by s."""
+    w = W.shock_tube_1d(steps=300)
+    ws = W.Workload(**{**w.__dict__, "n": w.n * scale, "eps": w.eps * scale})
+    ref, _ = oracle_run(ws, 300)
+    got, sim = gpu_run(ws, 300, prec)
+    st = sim.stats()
+    sim.close()
+    assert st["n_unphysical"] == 0
+    assert max(rel_errors(got, ref)) <= TOL[prec]
+    base, sim = gpu_run(w, 300, prec)
+    sim.close()
+    n, e, b = got
+    n0, e0, b0 = base
+    tol = 1e-11 if prec == "fp64" else TOL[prec]
+    assert max(rel_errors((n / scale, e / scale, b), (n0, e0, b0))) <= tol

@@ -80,20 +80,22 @@ def test_tachyon_fig5_setup(prec):
 def test_tachyon_strong_shock(prec):
     """The 1:16 strong shock with c_l = 10 (within the positivity bound of the
     f equilibria, beta* = 0.541), 1600 cells, 4000 steps at tau = 0.52: parity
-    with the oracle, and the star plateau against the exact solution.
+    with the oracle (FP64 1e-10, FP32 1e-4), and the star plateau against the
+    exact solution.
 
-    FP32 bound 2e-3 (measured 7e-4, at the shock front): at c_l = 10 the
-    velocity terms of the g equilibria (4 c_i.u / c_l^2 in Eq. equil2as) are
-    about 20x their rest term 1/(gamma^2 c_l^2), and they cancel in pairs in
-    the moments, so binary32 populations keep about one digit less than at
-    c_l = 1."""
+    At c_l = 10 the velocity terms of the g equilibria (4 c_i.u / c_l^2 in
+    Eq. equil2as) are about 20x their rest term, and the moments that drive
+    the flow are sums in which they cancel.  The FP32 path runs its
+    compensated collision for c_l > 1 (binary32 storage, the collision's
+    arithmetic carried in binary32 pairs); the plain binary32 collision
+    misses this bound by 7x (7e-4) on this run."""
     P0, T0, P1, T1 = 1 / 3, 1 / 3, 1 / 48, 1 / 6
     w = W.riemann_tube(P0, P1, T0, T1, cells=1598, tau=0.52, c_l=10.0, steps=4000)
     got, sim = gpu_run(w, w.steps, prec)
     assert sim.stats()["n_unphysical"] == 0
     sim.close()
     ref, _ = oracle_run(w, w.steps)
-    assert max(rel_errors(got, ref)) <= (1e-10 if prec == "fp64" else 2e-3)
+    assert max(rel_errors(got, ref)) <= (1e-10 if prec == "fp64" else 1e-4)
     sol = riemann.solve(3 * P0, P0 / T0, 3 * P1, P1 / T1)
     xi = _xi(w)
     plateau = (xi > sol.xi_tail + 0.05) & (xi < sol.v_shock - 0.05)

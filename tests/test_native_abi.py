@@ -57,6 +57,10 @@ def test_parameter_validation(native):
         N.make_params(4, 4, 4, 0.8, eos=N.RLB_EOS_GAMMA_LAW, eos_gamma=1.0),  # 1 < Gamma <= 2
         N.make_params(4, 4, 4, 0.8, eos=N.RLB_EOS_GAMMA_LAW, eos_gamma=2.5),
         N.make_params(4, 4, 4, 0.8, eos=N.RLB_EOS_GAMMA_LAW, eos_gamma=1.5, eos_mass=-1.0),
+        N.make_params(4, 4, 2, 0.8, zbc=N.RLB_ZBC_HALO),  # a z slab needs nz >= 3
+        N.make_params(4, 4, 4, 0.8, zbc=2),
+        N.make_params(4, 4, 4, 0.8, eos=N.RLB_EOS_GAMMA_LAW, eos_gamma=5 / 3, zbc=N.RLB_ZBC_HALO),
+        N.make_params(2145386497, 1, 1, 0.8),  # N > 2^31 - 2^21
     ]
     for p in bad:
         with pytest.raises(N.RLBError) as ei:
@@ -67,6 +71,12 @@ def test_parameter_validation(native):
     with pytest.raises(N.RLBError):
         N.rlb_workspace_bytes(p)
     N.rlb_state_layout(N.make_params(4, 4, 4, 0.8, eos=N.RLB_EOS_GAMMA_LAW, eos_gamma=5 / 3, eos_mass=0.5))
+    N.rlb_state_layout(N.make_params(4, 4, 3, 0.8, zbc=N.RLB_ZBC_HALO))
+    N.rlb_state_layout(N.make_params(2145386496, 1, 1, 0.8))  # N = 2^31 - 2^21
+    p = N.make_params(4, 4, 4, 0.8)
+    p.reserved = 1
+    with pytest.raises(N.RLBError):
+        N.rlb_state_layout(p)
     assert N.rlb_status_str(N.RLB_ERR_UNPHYSICAL) == "RLB_ERR_UNPHYSICAL"
 
 

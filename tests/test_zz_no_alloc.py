@@ -32,6 +32,25 @@ def _need_gpu():
         pytest.skip("needs a CUDA GPU")
 
 
+@pytest.fixture(scope="module", autouse=True)
+def _setup_call(_need_gpu):
+    """The entry point's documented set-up: its first call on the device (here
+    on a small FP64 periodic lattice) takes the scratch array's address and
+    loads every kernel it launches.  After it, no call of any precision or x
+    boundary may change the device's free memory."""
+    from paper_0912_2913_gb300 import RLB
+    from paper_0912_2913_gb300 import _native as N
+
+    w = tiny_workload(6, 5, 4, 0, seed=2)
+    sim = RLB.from_workload(w, "fp64", device="cuda:0").init_fields(w.n, w.eps, w.beta)
+    s = sim.state()
+    li, lo = torch.zeros_like(s), torch.zeros_like(s)
+    acc = torch.zeros(4, dtype=torch.float64, device="cuda")
+    N.rlb_adjoint_step_noalloc(sim.ctx, s, li, lo, acc[0:1], acc[1:4])
+    sim.sync()
+    sim.close()
+
+
 def _rel(a, b):
     a = a.double().cpu().numpy()
     b = b.double().cpu().numpy()
@@ -65,12 +84,12 @@ def test_noalloc_adjoint_step_matches_adjoint_step(case, prec):
     for call in range(2):
         N.rlb_adjoint_step(sim.ctx, state, la_in, la_out, acc_a[0:1], acc_a[1:4])
         torch.cuda.synchronize()
-        if call == 1:
-            free_before = torch.cuda.mem_get_info()[0]
+        # after the set-up call, no call allocates: also not the first one of
+        # this precision and x boundary (no kernel is loaded on demand)
+        free_before = torch.cuda.mem_get_info()[0]
         N.rlb_adjoint_step_noalloc(sim.ctx, state, lb_in, lb_out, acc_b[0:1], acc_b[1:4])
         sim.sync()
-        if call == 1:
-            assert torch.cuda.mem_get_info()[0] == free_before, "device memory changed across the call"
+        assert torch.cuda.mem_get_info()[0] == free_before, f"device memory changed across call {call + 1}"
         assert torch.isfinite(lb_out[:, :n]).all()
         assert _rel(lb_out[:, :n], la_out[:, :n]) <= TOL[prec], f"lambda_t differs after call {call + 1}"
         assert abs(acc_b[0].item() - acc_a[0].item()) <= TOL[prec] * max(abs(acc_a[0].item()), 1e-30)
