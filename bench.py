@@ -618,6 +618,41 @@ def precision_legs(w, prec, steps, peak, device, ms_fwd=None, adjoint=True):
     return legs
 
 
+def slab_leg(w, steps, peak, device, ms_whole, nslabs=4):
+    """The z-slab decomposition on one GPU: the workload cut into nslabs z
+    slabs (one context each, two halo planes), every step = the slab steps
+    + rlb_halo_exchange between neighbours.  MLUPS over the whole lattice's
+    collided cells; the exchange's own time from a run of exchanges alone."""
+    import torch
+
+    from paper_0912_2913_gb300 import _native as Nat
+    from paper_0912_2913_gb300.slabs import SlabLattice
+
+    lat = SlabLattice.from_workload(w, "fp32", nslabs=nslabs, device=device)
+    lat.init_fields(w.n, w.eps, w.beta, w.solid).step(3)
+    torch.cuda.synchronize()
+    st = lat.slabs[0].stream
+    a, b = _events(torch, st)
+    a.record(st)
+    lat.step(steps)
+    b.record(st)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    a.record(st)
+    for _ in range(steps):
+        lat.exchange()
+    b.record(st)
+    torch.cuda.synchronize()
+    ms_x = a.elapsed_time(b) / steps
+    lat.close()
+    del lat
+    torch.cuda.empty_cache()
+    cells = collided_cells(w)
+    return _leg(cells, ms, steps, BYTES_FWD["fp32"], peak,
+                {"slabs": nslabs, "exchange_ms_per_step": ms_x, "ratio_to_whole_lattice_step": (ms / steps) / ms_whole,
+                 "halo_bytes_per_step": 2 * 10 * w.nx * w.ny * 4 * nslabs})
+
+
 def sphere_legs(steps, grad_steps, peak, device, adjoint=True):
     """The 3D shock on a sphere as a leg of the box benchmark: FP32 forward,
     FP32 adjoint step and a whole FP32 gradient run."""
@@ -674,6 +709,7 @@ def run_ours(args):
             legs.update(precision_legs(w, "fp64", k_side, peak, device, adjoint=not args.no_adjoint))
             legs["fp64_gamma_law_forward"] = gamma_law_leg(w, k_side, device, peak,
                                                            legs["fp64_forward"]["ms_per_step"], cells)
+            legs["fp32_z_slabs"] = slab_leg(w, k_side * 2, peak, device, ms / args.steps)
             if args.workload == "sphere":
                 if not args.no_adjoint and args.grad_steps > 0:
                     legs["fp32_gradient_run"] = gradient_run_leg(w, args.grad_steps, device, ms / args.steps)

@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "rlb_collide.cuh"
 #include "rlb_device.cuh"
 
@@ -189,32 +191,49 @@ __global__ void __launch_bounds__(256, MINB) k_step_f32(const float* __restrict_
     cell_coords(g, idx, x, y, z);
     if (g.zhalo && (z == 0 || z == g.nz - 1)) return;  // z halo planes: filled by the exchange
     const I S = (I)g.S;
+    // I = unsigned: the f planes (0..18) and the g planes (19..37) are
+    // addressed from their own base pointers with unsigned 32-bit element
+    // offsets (for lattices with 38 S >= 2^31 and 19 S < 2^32), which costs
+    // no more address arithmetic than the int offsets.
+    constexpr bool SPLIT = std::is_same<I, unsigned>::value;
+    const float* __restrict__ Ag = SPLIT ? A + 19ll * g.S : A;
+    float* Bg = SPLIT ? B + 19ll * g.S : B;
+    const long long lim = (SPLIT ? 19ll : 38ll) * g.S;  // extent the checked builds test against
+    auto pq = [](int q) { return (SPLIT && q >= 19) ? q - 19 : q; };  // plane number within its base
+    auto abase = [&](int q) { return (SPLIT && q >= 19) ? Ag : A; };
     if (XBC != XBC_PERIODIC && (x == 0 || x == g.nx - 1)) {
         if (XBC == XBC_INFLOW_OUTFLOW && x == 0) {
 #pragma unroll
-            for (int q = 0; q < 38; ++q) B[RLB_CHK(q * S + idx, 38ll * S)] = __ldg(RLB_CHK_PTR(A, q * S + idx, 38ll * S));
+            for (int q = 0; q < 38; ++q)
+                ((SPLIT && q >= 19) ? Bg : B)[RLB_CHK(pq(q) * S + idx, lim)] = __ldg(RLB_CHK_PTR(abase(q), pq(q) * S + idx, lim));
         }
         return;
     }
     const PullOffsets o(g, x, y, z);
     const int dup = (XBC != XBC_PERIODIC && x == g.nx - 2) ? 1 : ((XBC == XBC_OUTFLOW_BOTH && x == 1) ? -1 : 0);
     float* Bc = B + idx;
+    float* Bgc = Bg + idx;
     auto put = [&](int q, float v) {
-        Bc[RLB_CHK_OFF(q * S, idx, 38ll * S)] = v;
-        if (dup) Bc[RLB_CHK_OFF(q * S + dup, idx, 38ll * S)] = v;
+        float* b = (SPLIT && q >= 19) ? Bgc : Bc;
+        b[RLB_CHK_OFF(pq(q) * S, idx, lim)] = v;
+        // the outflow copy: dup (+-1) moves the pointer, so that an unsigned
+        // offset never has to hold a negative value
+        if (dup) (b + dup)[RLB_CHK_OFF(pq(q) * S, idx + dup, lim)] = v;
     };
-    if (SOLID && is_solid(__ldg(RLB_CHK_PTR(A, 19 * S + idx, 38ll * S)))) {  // the cell itself is solid: keep the marker
+    if (SOLID && is_solid(__ldg(RLB_CHK_PTR(abase(19), pq(19) * S + idx, lim)))) {  // the cell itself is solid: keep the marker
         const float m = solid_marker_f();
 #pragma unroll
-        for (int q = 0; q < 38; ++q) Bc[RLB_CHK_OFF(q * S, idx, 38ll * S)] = m;
+        for (int q = 0; q < 38; ++q) ((SPLIT && q >= 19) ? Bgc : Bc)[RLB_CHK_OFF(pq(q) * S, idx, lim)] = m;
         return;
     }
     if (PREF) {
 #pragma unroll
-        for (int i = 0; i < 19; ++i) asm volatile("prefetch.global.L2 [%0];" ::"l"(RLB_CHK_PTR(A, i * S + idx + o.src(i), 38ll * S)));
+        for (int i = 0; i < 19; ++i) asm volatile("prefetch.global.L2 [%0];" ::"l"(RLB_CHK_PTR(A, i * S + idx + o.src(i), lim)));
     }
-    auto fetch = [&](int q, int i) { return __ldg(RLB_CHK_PTR(A, q * S + idx + o.src(i), 38ll * S)); };
-    auto bounce = [&](int q, int i) { return __ldg(RLB_CHK_PTR(A, (q - i + opp(i)) * S + idx, 38ll * S)); };  // link bounce-back
+    auto fetch = [&](int q, int i) { return __ldg(RLB_CHK_PTR(abase(q), pq(q) * S + idx + o.src(i), lim)); };
+    auto bounce = [&](int q, int i) {  // link bounce-back
+        return __ldg(RLB_CHK_PTR(abase(q), (pq(q) - i + opp(i)) * S + idx, lim));
+    };
     bool unphys, nonpos;
     if (COMP)
         collide_cell_f32c<SOLID>(fetch, bounce, put, c, unphys, nonpos);
@@ -536,12 +555,16 @@ static void launch_step_t(int prec, const Geom& g, const Phys& ph, const void* A
         const unsigned nb = blocks_for(g.N, tb);
         const int cs = count ? 1 : 0;
         const bool idx32 = 38 * g.S < (1ll << 31);
+        const bool split32 = !idx32 && 19 * g.S < (1ll << 32);  // unsigned offsets per population set
         if (ph.c_l > 1.0) {
             // lattice speeds above 1: the compensated collision (one launch
             // shape; the TMA-staged and tuning variants use the binary32 one)
             if (idx32)
                 k_step_f32<XBC, SOLID, 2, false, int, true><<<nb, tb, 0, st>>>((const float*)A, (float*)B, g, c, cnt, cs,
                                                                                  step_index);
+            else if (split32)
+                k_step_f32<XBC, SOLID, 2, false, unsigned, true><<<nb, tb, 0, st>>>((const float*)A, (float*)B, g, c, cnt,
+                                                                                      cs, step_index);
             else
                 k_step_f32<XBC, SOLID, 2, false, long long, true><<<nb, tb, 0, st>>>((const float*)A, (float*)B, g, c,
                                                                                        cnt, cs, step_index);
@@ -555,12 +578,18 @@ static void launch_step_t(int prec, const Geom& g, const Phys& ph, const void* A
             case 1:
                 if (idx32)
                     k_step_f32<XBC, SOLID, 3, true, int><<<nb, tb, 0, st>>>((const float*)A, (float*)B, g, c, cnt, cs, step_index);
+                else if (split32)
+                    k_step_f32<XBC, SOLID, 3, true, unsigned><<<nb, tb, 0, st>>>((const float*)A, (float*)B, g, c, cnt, cs,
+                                                                               step_index);
                 else
                     k_step_f32<XBC, SOLID, 3, true><<<nb, tb, 0, st>>>((const float*)A, (float*)B, g, c, cnt, cs, step_index);
                 break;
             case 2:
                 if (idx32)
                     k_step_f32<XBC, SOLID, 4, false, int><<<nb, tb, 0, st>>>((const float*)A, (float*)B, g, c, cnt, cs, step_index);
+                else if (split32)
+                    k_step_f32<XBC, SOLID, 4, false, unsigned><<<nb, tb, 0, st>>>((const float*)A, (float*)B, g, c, cnt, cs,
+                                                                                step_index);
                 else
                     k_step_f32<XBC, SOLID, 4, false><<<nb, tb, 0, st>>>((const float*)A, (float*)B, g, c, cnt, cs, step_index);
                 break;
