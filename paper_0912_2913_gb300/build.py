@@ -22,7 +22,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["rlb_forward.cu", "rlb_stream.cu", "rlb_adjoint.cu", "rlb_eos.cu", "rlb_api.cu"]
+SOURCES = ["rlb_forward.cu", "rlb_stream.cu", "rlb_adjoint.cu", "rlb_eos.cu", "rlb_f64df.cu", "rlb_api.cu"]
 HEADERS = ["rlb_internal.h", "rlb_device.cuh", "rlb_collide.cuh", "rlb_tma.cuh", "rlb_dfloat.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fmad=false: no implicit a*b+c contraction, so every kernel computes exactly

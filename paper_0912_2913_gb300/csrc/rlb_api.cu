@@ -237,6 +237,11 @@ rlb_status rlb_create(const rlb_params* p, void* stream, void* workspace, size_t
         g.adj_idx64 = (a64 && a64[0] == '1') ? 1 : 0;
         const char* pb = getenv("RLB_PIPE_BLOCKS");
         g.pipe_blocks = pb ? atoi(pb) : 3;
+        // RLB_F64_ARITH=df: the FP64 step with its arithmetic in compensated
+        // binary32 pairs (binary64 storage and recovery root; an ablation of
+        // the all-FP64 step, which stays the default)
+        const char* fa = getenv("RLB_F64_ARITH");
+        g.f64df = (fa && fa[0] == 'd' && fa[1] == 'f') ? 1 : 0;
     }
     Phys& ph = c->ph;
     ph.tau = p->tau;

@@ -64,6 +64,29 @@ __device__ __forceinline__ dfl df_of(double x) {
     return {h, d2f(x - f2d(h))};
 }
 
+// Split of a binary64 value into a pair on the integer pipe (no FP64
+// instruction): h = x rounded to binary32 (d2f), and the remainder x - h,
+// exact in binary64 as the signed integer R of the 29 mantissa bits below
+// h's precision (minus 2^29 when h was rounded up) times 2^(E - 52), rounded
+// once more to binary32 (I2F), so h + l carries 48 of x's 53 significant
+// bits.  Valid while both parts are binary32 normals: |x| between about
+// 2^-100 and 2^127; zero stays zero.
+__device__ __forceinline__ dfl df_split(double x) {
+    const float h = d2f(x);
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const int e = (int)((hi >> 20) & 0x7FFu);  // biased exponent of x
+    const int r29 = (int)(lo & 0x1FFFFFFFu);
+    const int up = (r29 > 0x10000000) || (r29 == 0x10000000 && ((lo >> 29) & 1u));
+    const int R = r29 - (up << 29);           // x - h = +-R 2^(e - 1075)
+    const float fr = __int2float_rn(R);
+    // scale by 2^(e - 1075) on the exponent field; the sign of x
+    const unsigned b = __float_as_uint(fr);
+    const unsigned scaled = (b + (unsigned)((e - 1075) * (1 << 23))) ^ (hi & 0x80000000u);
+    const int eb = (int)((b >> 23) & 0xFFu) + (e - 1075);  // biased exponent of l
+    const float l = (R == 0 || eb <= 0) ? 0.0f : __uint_as_float(scaled);
+    return {h, l};
+}
+
 // h + l in binary64 (exact for a normalised pair).
 __device__ __forceinline__ double df_dbl(dfl x) { return f2d(x.h) + f2d(x.l); }
 

@@ -547,6 +547,10 @@ static void launch_step_t(int prec, const Geom& g, const Phys& ph, const void* A
                           long long step_index, cudaStream_t st) {
     if (prec == 0) {
         const int tb = step_block(g.N, 128);
+        if (g.f64df) {
+            launch_step_f64_df(g, ph, A, B, cnt, count, step_index, st, tb);
+            return;
+        }
         k_step_f64<XBC, SOLID><<<blocks_for(g.N, tb), tb, 0, st>>>((const double*)A, (double*)B, g, ph, cnt,
                                                                     count ? 1 : 0, step_index);
     } else {

@@ -41,6 +41,7 @@ struct Geom {
     int adj_pipe;  // FP32 adjoint kernel: 0 one cell per thread, 1 persistent, 2 staged (tuning)
     int adj_idx64;  // 1: 64-bit element offsets in the staged adjoint even where 32 bits suffice (testing)
     int zhalo;      // 1: planes z = 0 and z = nz-1 are halo copies, not updated by a step
+    int f64df;      // 1: the FP64 step computes in compensated binary32 pairs (ablation)
 };
 
 // Physical parameters, with the derived constants the kernels use.
@@ -76,6 +77,9 @@ cudaError_t launch_step(int prec, const Geom& g, const Phys& ph, const void* A, 
                         bool count, long long step_index, cudaStream_t stream);
 cudaError_t launch_macro(int prec, const Geom& g, const Phys& ph, const void* A, double* n, double* eps,
                          double* beta, Counters cnt, cudaStream_t stream);
+// FP64 step with its arithmetic in compensated binary32 pairs (rlb_f64df.cu).
+cudaError_t launch_step_f64_df(const Geom& g, const Phys& ph, const void* A, void* B, Counters cnt, bool count,
+                               long long step_index, cudaStream_t stream, int threads);
 // TMA-staged FP32 step; returns cudaErrorNotSupported when the lattice does
 // not meet its alignment / shared-memory conditions (caller falls back).
 cudaError_t launch_step_f32_tma(const Geom& g, const Dev32& c, const float* A, float* B, Counters cnt, bool count,
