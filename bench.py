@@ -371,6 +371,26 @@ def gamma_law_leg(w, steps, device, peak, ms_eps3p, cells):
     return leg
 
 
+def f64df_leg(w, steps, device, peak, ms_fp64, cells):
+    """The FP64-storage step with its arithmetic in compensated binary32
+    pairs (RLB_F64_ARITH=df, the measured ablation of the all-FP64 step)."""
+    import torch
+
+    from paper_0912_2913_gb300 import RLB
+
+    os.environ["RLB_F64_ARITH"] = "df"
+    try:
+        sim = RLB.from_workload(w, "fp64", device=device).init_fields(w.n, w.eps, w.beta, w.solid)
+    finally:
+        os.environ.pop("RLB_F64_ARITH", None)
+    ms, _ = time_forward(sim, steps, 3, 1, device)
+    sim.close()
+    torch.cuda.empty_cache()
+    return _leg(cells, ms, steps, BYTES_FWD["fp64"], peak,
+                {"arithmetic": "compensated binary32 pairs, binary64 storage and recovery root",
+                 "ratio_to_fp64_step": (ms / steps) / ms_fp64})
+
+
 def shock_tube_graph_leg(device, steps_per_graph=100, replays=20):
     """The launch-bound 1D shock tube (1600 cells, FP64): microseconds per step
     with one rlb_step call per 1000 steps, and with steps_per_graph steps
@@ -710,6 +730,8 @@ def run_ours(args):
             legs["fp64_gamma_law_forward"] = gamma_law_leg(w, k_side, device, peak,
                                                            legs["fp64_forward"]["ms_per_step"], cells)
             legs["fp32_z_slabs"] = slab_leg(w, k_side * 2, peak, device, ms / args.steps)
+            legs["fp64_df_arith_forward"] = f64df_leg(w, k_side, device, peak, legs["fp64_forward"]["ms_per_step"],
+                                                      cells)
             if args.workload == "sphere":
                 if not args.no_adjoint and args.grad_steps > 0:
                     legs["fp32_gradient_run"] = gradient_run_leg(w, args.grad_steps, device, ms / args.steps)
