@@ -254,6 +254,20 @@ rlb_status rlb_create(const rlb_params* p, void* stream, void* workspace, size_t
     for (int a = 0; a < 3; ++a) ph.beta_in[a] = p->beta_in[a];
     ph.n_ref = p->n_ref;
     ph.eps_ref = p->eps_ref;
+    for (int cl = 0; cl < 2; ++cl) {
+        const double w = cl == 0 ? 1.0 / 18.0 : 1.0 / 36.0;
+        ph.c_k1[cl] = ph.omega * w * ph.inv_cl2;
+        ph.c_k2[cl] = 6.0 * ph.omega * w * ph.inv_cl2;
+        ph.c_k3[cl] = 4.0 * ph.omega * w * ph.inv_cl;
+        ph.c_fs[cl] = ph.omega * w;
+        ph.c_fa[cl] = 3.0 * ph.omega * w * ph.inv_cl;
+    }
+    ph.c_f0 = ph.omega / 3.0;
+    ph.c_g0[0] = 4.0 * ph.omega / 3.0;
+    ph.c_g0[1] = -(ph.omega / 3.0) * (2.0 * ph.inv_cl2 + 1.0);
+    ph.c_g0[2] = -2.0 * (ph.omega / 3.0) * ph.inv_cl2;
+    ph.m3cl2 = -3.0 * p->c_l * p->c_l;
+    ph.three_cl = 3.0 * p->c_l;
     ph.eos = p->eos;
     ph.eos_gamma = p->eos == RLB_EOS_GAMMA_LAW ? p->eos_gamma : 4.0 / 3.0;
     ph.eos_mass = p->eos == RLB_EOS_GAMMA_LAW ? p->eos_mass : 0.0;
@@ -362,19 +376,20 @@ rlb_status rlb_init_fields(rlb_ctx* c, const double* n, const double* eps, const
 }
 
 // Launch variants of the FP32 step compute bit-identical results; which one
-// is fastest depends on the lattice (measured: the 64-register one on the
-// 200x100x100 sphere, the 80-register one with L2 prefetch on a 512^3 box).
-// The first FP32 rlb_step times both on the context's second buffer (which
-// the step then overwrites) and keeps the faster.  This first call
-// synchronises the stream once.
+// is fastest depends on the lattice.  The candidates: 2 (256-thread blocks,
+// 64 registers), 7 and 8 (the f populations loaded before the g arithmetic,
+// 128 x 7 blocks at 72 registers, 64 x 12 at 80; measured fastest on the
+// 512^3 box and the 200x100x100 sphere).  The first FP32 rlb_step times
+// each on the context's second buffer (which the step then overwrites) and
+// keeps the fastest.  This first call synchronises the stream once.
 static rlb_status autotune_f32(rlb_ctx* c) {
-    const int cand[2] = {1, 2};
+    const int cand[3] = {2, 7, 8};
     float best = 1e30f;
-    int pick = 1;
+    int pick = 2;
     cudaEvent_t e0, e1;
     RLB_CUDA(c, cudaEventCreate(&e0), "event");
     RLB_CUDA(c, cudaEventCreate(&e1), "event");
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < 3; ++k) {
         c->g.variant = cand[k];
         cudaError_t e = launch_step(c->p.prec, c->g, c->ph, c->A, c->B, c->cnt, false, 0, c->stream);
         if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
@@ -411,7 +426,7 @@ rlb_status rlb_step(rlb_ctx* c, int32_t nsteps) {
             rlb_status s = autotune_f32(c);
             if (s != RLB_OK) return s;
         } else {
-            c->g.variant = 1;
+            c->g.variant = 7;
         }
     }
     for (int32_t t = 0; t < nsteps; ++t) {
@@ -433,7 +448,7 @@ rlb_status rlb_step_into(rlb_ctx* c, const void* src, void* dst) {
     Nvtx nvtx_("rlb_step_into");
     RLB_LATCHED(c);
     if (!src || !dst || src == dst) return fail(c, RLB_ERR_ARG, "src and dst must be distinct device buffers");
-    if (c->g.variant < 0) c->g.variant = 1;
+    if (c->g.variant < 0) c->g.variant = 7;  // untuned: the shape measured fastest on the benchmark lattices
     return after_launch(c,
                         c->ph.eos ? launch_step_eos(c->g, c->ph, src, dst, c->cnt, false, 0, c->stream)
                                   : launch_step(c->p.prec, c->g, c->ph, src, dst, c->cnt, false, 0, c->stream),
@@ -445,7 +460,7 @@ rlb_status rlb_step_into_counted(rlb_ctx* c, const void* src, void* dst) {
     RLB_LATCHED(c);
     if (!src || !dst || src == dst) return fail(c, RLB_ERR_ARG, "src and dst must be distinct device buffers");
     if (!c->inited) return fail(c, RLB_ERR_STATE, "rlb_step_into_counted before rlb_init_fields");
-    if (c->g.variant < 0) c->g.variant = 1;
+    if (c->g.variant < 0) c->g.variant = 7;  // untuned: the shape measured fastest on the benchmark lattices
     rlb_status s = after_launch(c,
                                 c->ph.eos ? launch_step_eos(c->g, c->ph, src, dst, c->cnt, true, c->steps, c->stream)
                                           : launch_step(c->p.prec, c->g, c->ph, src, dst, c->cnt, true, c->steps,

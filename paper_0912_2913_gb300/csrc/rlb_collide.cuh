@@ -43,12 +43,20 @@ __device__ __forceinline__ void gather_phase(float* v, int base, Fetch fetch, Bo
     }
 }
 
-template <bool SOLID, class Fetch, class Bounce, class Put>
+// EARLYF: the f populations are loaded into registers before the g phase's
+// arithmetic, so that their loads are in flight during it (the same values,
+// the same arithmetic; more registers per thread).
+template <bool SOLID, class Fetch, class Bounce, class Put, bool EARLYF = false>
 __device__ __forceinline__ void collide_cell_f32(Fetch fetch, Bounce bounce, Put put, const Dev32& c, bool& unphys,
                                                  bool& nonpos) {
     const float om = c.omega;
     // ---- phase 1: energy-momentum populations g_i (they alone fix eps, beta) ----
     float gg[19];
+    float f[19];
+    if (EARLYF) {
+#pragma unroll
+        for (int i = 0; i < 19; ++i) f[i] = fetch(i, i);
+    }
     gather_phase<SOLID>(gg, 19, fetch, bounce);
     float dE = gg[0], d[9];
 #pragma unroll
@@ -98,8 +106,20 @@ __device__ __forceinline__ void collide_cell_f32(Fetch fetch, Bounce bounce, Put
         }
     }
     // ---- phase 2: number populations f_i ----
-    float f[19];
-    gather_phase<SOLID>(f, 0, fetch, bounce);
+    if (EARLYF) {
+        if (SOLID) {  // the markers test of gather_phase, on the values already loaded
+            float s = f[0];
+#pragma unroll
+            for (int i = 1; i < 19; ++i) s += f[i];
+            if (isnan(s)) {
+#pragma unroll
+                for (int i = 1; i < 19; ++i)
+                    if (is_solid(f[i])) f[i] = bounce(i, i);
+            }
+        }
+    } else {
+        gather_phase<SOLID>(f, 0, fetch, bounce);
+    }
     float dS = f[0];
 #pragma unroll
     for (int i = 1; i < 19; ++i) dS += f[i];

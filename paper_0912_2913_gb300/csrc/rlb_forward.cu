@@ -73,18 +73,16 @@ __global__ void __launch_bounds__(128) k_step_f64(const double* __restrict__ A, 
             }
         }
     }
-    double sf, E, mx, my, mz;
-    moments_pairs(f, gg, sf, E, mx, my, mz);
-    mx *= ph.c_l;
-    my *= ph.c_l;
-    mz *= ph.c_l;
+    // d = M / c_l (the pair differences summed along each axis)
+    double sf, E, dx, dy, dz;
+    moments_pairs(f, gg, sf, E, dx, dy, dz);
     // Recovery with eps = 3P: eps = -E + sqrt(4E^2 - 3M^2), beta = 3M/(3E + eps).
     // Square root and reciprocals from binary32 seeds (converted on the integer
     // pipe, valid for any exponent of the argument) with two FP64 Newton
     // corrections each: full double accuracy at a fraction of the IEEE
     // sequences' cost on this GPU's FP64 pipe.
-    const double m2 = fma(mx, mx, fma(my, my, mz * mz));
-    const double disc = fma(4.0 * E, E, -3.0 * m2);
+    const double m2 = fma(dx, dx, fma(dy, dy, dz * dz));  // |M|^2 / c_l^2
+    const double disc = fma(4.0 * E, E, ph.m3cl2 * m2);   // 4E^2 - 3|M|^2
     double ys, hs;
     rsqrt_seed(disc, ys, hs);
     double sq = disc * ys;
@@ -95,41 +93,40 @@ __global__ void __launch_bounds__(128) k_step_f64(const double* __restrict__ A, 
     double rD = rcp_seed(D);
     rD = fma(rD, fma(-D, rD, 1.0), rD);
     rD = fma(rD, fma(-D, rD, 1.0), rD);
-    const double r3 = 3.0 * rD;
-    const double bx = mx * r3, by = my * r3, bz = mz * r3;
+    const double r3 = ph.three_cl * rD;  // beta = 3 M / D = 3 c_l d / D
+    const double bx = dx * r3, by = dy * r3, bz = dz * r3;
     const double b2 = fma(bx, bx, fma(by, by, bz * bz));
     const double omb2 = 1.0 - b2;
     double gam2 = rcp_seed(omb2);
     gam2 = fma(gam2, fma(-omb2, gam2, 1.0), gam2);
     gam2 = fma(gam2, fma(-omb2, gam2, 1.0), gam2);
     const bool unphys = !(pos_finite(sf) && pos_finite(E) && nonneg_finite(disc) && pos_finite(eps) && below_one(b2));
-    const bool nonpos = nonpositive_eq((float)bx, (float)by, (float)bz, (float)ph.c_l);
+    // beta rounded to binary32 on the integer pipe (the same rounding as a conversion)
+    const bool nonpos = nonpositive_eq(d2f(bx), d2f(by), d2f(bz), (float)ph.c_l);
 
-    const double om = ph.omega, omw = 1.0 - ph.omega;
+    // The relaxed values omega eq + (1 - omega) h, with omega and the weights
+    // folded into per-run constants (Phys::c_*):
+    //   f^eq_i = w_i S_f (1 + 3 q_i / c_l)     (Eq. equil1s with n gamma = S_f)
+    //   g^eq_i = w_i [eps/c_l^2 + eps gamma^2 (6 q^2/c_l^2 - 2 b2/c_l^2)] +- w_i eps gamma^2 4 q / c_l
+    //   g_0^eq = w_0 [4 eps gamma^2 - eps (2 + c_l^2)/c_l^2 - 2 eps gamma^2 b2/c_l^2]   (Eq. equil2bs)
+    const double omw = 1.0 - ph.omega;
     const double q[9] = {bx, by, bz, bx + by, bx - by, bx + bz, bx - bz, by + bz, by - bz};
-    // f^eq_i = w_i S_f (1 + 3 q_i / c_l)     (Eq. equil1s with n gamma = S_f)
-    const double fs1 = om * (1.0 / 18.0) * sf, fs2 = om * (1.0 / 36.0) * sf;
-    const double fa1 = 3.0 * om * sf * ph.inv_cl * (1.0 / 18.0), fa2 = 3.0 * om * sf * ph.inv_cl * (1.0 / 36.0);
-    // g^eq_i = w_i [eps/c_l^2 + eps gamma^2 (6 q^2/c_l^2 - 2 b2/c_l^2)] +- w_i eps gamma^2 4 q / c_l
     const double eg = eps * gam2;
-    const double k1 = om * (eps - 2.0 * eg * b2) * ph.inv_cl2;
-    const double k2 = 6.0 * om * eg * ph.inv_cl2;
-    const double k3 = 4.0 * om * eg * ph.inv_cl;
-    const double k1w[2] = {k1 * (1.0 / 18.0), k1 * (1.0 / 36.0)};
-    const double k2w[2] = {k2 * (1.0 / 18.0), k2 * (1.0 / 36.0)};
-    const double k3w[2] = {k3 * (1.0 / 18.0), k3 * (1.0 / 36.0)};
+    const double egb2 = eg * b2;
+    const double t = fma(-2.0, egb2, eps);  // eps - 2 eg b2
+    const double k1w[2] = {t * ph.c_k1[0], t * ph.c_k1[1]};
+    const double k2w[2] = {eg * ph.c_k2[0], eg * ph.c_k2[1]};
+    const double k3w[2] = {eg * ph.c_k3[0], eg * ph.c_k3[1]};
+    const double fsw[2] = {sf * ph.c_fs[0], sf * ph.c_fs[1]};
+    const double faw[2] = {sf * ph.c_fa[0], sf * ph.c_fa[1]};
     double outf[19], outg[19];
-    outf[0] = fma(omw, f[0], om * kW0 * sf);
-    // g_0^eq = w_0 [4 eps gamma^2 - eps (2 + c_l^2)/c_l^2 - 2 eps gamma^2 b2/c_l^2]   (Eq. equil2bs)
-    const double g0eq = kW0 * (4.0 * eg - eps * (2.0 * ph.inv_cl2 + 1.0) - 2.0 * eg * b2 * ph.inv_cl2);
-    outg[0] = fma(omw, gg[0], om * g0eq);
+    outf[0] = fma(omw, f[0], sf * ph.c_f0);
+    outg[0] = fma(omw, gg[0], fma(eg, ph.c_g0[0], fma(eps, ph.c_g0[1], egb2 * ph.c_g0[2])));
 #pragma unroll
     for (int p = 0; p < 9; ++p) {
         const int cl = p < 3 ? 0 : 1;
-        const double fsym = cl == 0 ? fs1 : fs2;
-        const double fa = cl == 0 ? fa1 : fa2;
-        outf[2 * p + 1] = fma(omw, f[2 * p + 1], fma(fa, q[p], fsym));
-        outf[2 * p + 2] = fma(omw, f[2 * p + 2], fma(-fa, q[p], fsym));
+        outf[2 * p + 1] = fma(omw, f[2 * p + 1], fma(faw[cl], q[p], fsw[cl]));
+        outf[2 * p + 2] = fma(omw, f[2 * p + 2], fma(-faw[cl], q[p], fsw[cl]));
         const double gsym = fma(k2w[cl], q[p] * q[p], k1w[cl]);
         outg[2 * p + 1] = fma(omw, gg[2 * p + 1], fma(k3w[cl], q[p], gsym));
         outg[2 * p + 2] = fma(omw, gg[2 * p + 2], fma(-k3w[cl], q[p], gsym));
@@ -182,9 +179,12 @@ __global__ void __launch_bounds__(128) k_step_f64(const double* __restrict__ A, 
 // instructions: measured +2 % / +6 % for the two shapes the first step picks
 // from on the 200x100x100 sphere), else long long.
 // COMP: the compensated collision (collide_cell_f32c), run for c_l > 1.
-template <int XBC, bool SOLID, int MINB, bool PREF, typename I = long long, bool COMP = false>
-__global__ void __launch_bounds__(256, MINB) k_step_f32(const float* __restrict__ A, float* __restrict__ B, Geom g,
-                                                        Dev32 c, Counters cnt, int count, long long step_index) {
+// EARLY: the f populations are loaded before the g phase's arithmetic.
+// TB: threads per block the register budget is cut for.
+template <int XBC, bool SOLID, int MINB, bool PREF, typename I = long long, bool COMP = false, bool EARLY = false,
+          int TB = 256>
+__global__ void __launch_bounds__(TB, MINB) k_step_f32(const float* __restrict__ A, float* __restrict__ B, Geom g,
+                                                       Dev32 c, Counters cnt, int count, long long step_index) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= g.N) return;
     int x, y, z;
@@ -214,11 +214,16 @@ __global__ void __launch_bounds__(256, MINB) k_step_f32(const float* __restrict_
     float* Bc = B + idx;
     float* Bgc = Bg + idx;
     auto put = [&](int q, float v) {
-        float* b = (SPLIT && q >= 19) ? Bgc : Bc;
-        b[RLB_CHK_OFF(pq(q) * S, idx, lim)] = v;
-        // the outflow copy: dup (+-1) moves the pointer, so that an unsigned
-        // offset never has to hold a negative value
-        if (dup) (b + dup)[RLB_CHK_OFF(pq(q) * S, idx + dup, lim)] = v;
+        if constexpr (SPLIT) {
+            float* b = q >= 19 ? Bgc : Bc;
+            b[RLB_CHK_OFF(pq(q) * S, idx, lim)] = v;
+            // the outflow copy: dup (+-1) moves the pointer, so that the
+            // unsigned offset never has to hold a negative value
+            if (dup) (b + dup)[RLB_CHK_OFF(pq(q) * S, idx + dup, lim)] = v;
+        } else {
+            Bc[RLB_CHK_OFF(q * S, idx, 38ll * S)] = v;
+            if (dup) Bc[RLB_CHK_OFF(q * S + dup, idx, 38ll * S)] = v;
+        }
     };
     if (SOLID && is_solid(__ldg(RLB_CHK_PTR(abase(19), pq(19) * S + idx, lim)))) {  // the cell itself is solid: keep the marker
         const float m = solid_marker_f();
@@ -230,15 +235,24 @@ __global__ void __launch_bounds__(256, MINB) k_step_f32(const float* __restrict_
 #pragma unroll
         for (int i = 0; i < 19; ++i) asm volatile("prefetch.global.L2 [%0];" ::"l"(RLB_CHK_PTR(A, i * S + idx + o.src(i), lim)));
     }
-    auto fetch = [&](int q, int i) { return __ldg(RLB_CHK_PTR(abase(q), pq(q) * S + idx + o.src(i), lim)); };
+    auto fetch = [&](int q, int i) {
+        if constexpr (SPLIT)
+            return __ldg(RLB_CHK_PTR(abase(q), pq(q) * S + idx + o.src(i), lim));
+        else
+            return __ldg(RLB_CHK_PTR(A, q * S + idx + o.src(i), 38ll * S));
+    };
     auto bounce = [&](int q, int i) {  // link bounce-back
-        return __ldg(RLB_CHK_PTR(abase(q), (pq(q) - i + opp(i)) * S + idx, lim));
+        if constexpr (SPLIT)
+            return __ldg(RLB_CHK_PTR(abase(q), (pq(q) - i + opp(i)) * S + idx, lim));
+        else
+            return __ldg(RLB_CHK_PTR(A, (q - i + opp(i)) * S + idx, 38ll * S));
     };
     bool unphys, nonpos;
     if (COMP)
         collide_cell_f32c<SOLID>(fetch, bounce, put, c, unphys, nonpos);
     else
-        collide_cell_f32<SOLID>(fetch, bounce, put, c, unphys, nonpos);
+        collide_cell_f32<SOLID, decltype(fetch), decltype(bounce), decltype(put), EARLY>(fetch, bounce, put, c, unphys,
+                                                                                        nonpos);
     if (count) count_flags(cnt, unphys, nonpos, (unsigned long long)step_index * (unsigned long long)g.N + idx);
 }
 
@@ -598,6 +612,29 @@ static void launch_step_t(int prec, const Geom& g, const Phys& ph, const void* A
                     k_step_f32<XBC, SOLID, 4, false><<<nb, tb, 0, st>>>((const float*)A, (float*)B, g, c, cnt, cs, step_index);
                 break;
             case 3: k_step_f32<XBC, SOLID, 4, true><<<nb, tb, 0, st>>>((const float*)A, (float*)B, g, c, cnt, cs, step_index); break;
+            case 6:
+            case 7:
+            case 8: {
+                // the f populations loaded before the g arithmetic (EARLY), in
+                // blocks of 128 threads x 6 or 7 per SM or 64 x 12 (80, 72 and
+                // 80 registers)
+                const float* a = (const float*)A;
+                float* b = (float*)B;
+                const int v = g.variant;
+                const int t = v == 8 ? (tb < 64 ? tb : 64) : (tb < 128 ? tb : 128);
+                const unsigned n = blocks_for(g.N, t);
+#define RLB_EARLY_LAUNCH(MB, TBK)                                                                                        \
+    do {                                                                                                                 \
+        if (idx32) k_step_f32<XBC, SOLID, MB, false, int, false, true, TBK><<<n, t, 0, st>>>(a, b, g, c, cnt, cs, step_index); \
+        else if (split32) k_step_f32<XBC, SOLID, MB, false, unsigned, false, true, TBK><<<n, t, 0, st>>>(a, b, g, c, cnt, cs, step_index); \
+        else k_step_f32<XBC, SOLID, MB, false, long long, false, true, TBK><<<n, t, 0, st>>>(a, b, g, c, cnt, cs, step_index); \
+    } while (0)
+                if (v == 6) RLB_EARLY_LAUNCH(6, 128);
+                else if (v == 7) RLB_EARLY_LAUNCH(7, 128);
+                else RLB_EARLY_LAUNCH(12, 64);
+#undef RLB_EARLY_LAUNCH
+                break;
+            }
             case 4:
             case 5: {
                 unsigned grid = (unsigned)sm_count() * (unsigned)(g.pipe_blocks > 0 ? g.pipe_blocks : 3);

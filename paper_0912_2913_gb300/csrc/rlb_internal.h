@@ -52,6 +52,13 @@ struct Phys {
     double n_ref, eps_ref;  // FP32 deviation reference (beta = 0)
     int eos;                // 0: eps = 3P; 1: P = (eos_gamma - 1)(eps - n eos_mass)
     double eos_gamma, eos_mass;
+    // Products of the run's constants that the FP64 step multiplies its
+    // per-cell values by, formed once on the host (w_cl: the pair weights
+    // 1/18, 1/36; w0 = 1/3): omega w_cl / c_l^2, 6 omega w_cl / c_l^2,
+    // 4 omega w_cl / c_l, omega w_cl, 3 omega w_cl / c_l, omega w0, and for
+    // omega g_0^eq: 4 omega w0, -omega w0 (2/c_l^2 + 1), -2 omega w0 / c_l^2;
+    // -3 c_l^2 and 3 c_l for the recovery from M / c_l.
+    double c_k1[2], c_k2[2], c_k3[2], c_fs[2], c_fa[2], c_f0, c_g0[3], m3cl2, three_cl;
 };
 
 // Binary32 constants of the FP32 deviation step.

@@ -267,7 +267,8 @@ def test_tma_staged_step_equals_plain_step(shape, monkeypatch):
 
     states = []
     for tma, var, minb in (("1", "0", "2"), ("1", "0", "3"), ("0", "0", "2"), ("0", "1", "2"), ("0", "2", "2"),
-                           ("0", "3", "2"), ("0", "4", "2"), ("0", "5", "2")):
+                           ("0", "3", "2"), ("0", "4", "2"), ("0", "5", "2"), ("0", "6", "2"), ("0", "7", "2"),
+                           ("0", "8", "2")):
         monkeypatch.setenv("RLB_TMA", tma)
         monkeypatch.setenv("RLB_F32_VARIANT", var)
         monkeypatch.setenv("RLB_TMA_MINB", minb)
