@@ -628,14 +628,29 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// I: index type of the element offsets, int when 38 S < 2^31 (fewer address
-// instructions), else long long.
-template <int XBC, typename I>
+// Base address of each of the 38 planes of the three buffers, a kernel
+// parameter: with every plane number a compile-time constant after
+// unrolling, an address is a 32-bit cell offset added to a uniform base.
+struct PlaneTab {
+    const float* a[38];
+    const float* l[38];
+    float* o[38];
+};
+
+// Every address of a cell's populations is its plane's base from the table
+// plus a 32-bit cell offset (N < 2^31): the fewest address instructions at any
+// accepted lattice size.
+template <int XBC>
 __global__ void __launch_bounds__(kStageThreads, 3)
     k_adjoint_step_staged(const float* __restrict__ A, const float* __restrict__ Lin, float* __restrict__ Lout,
-                          Geom g, Phys ph, AdjConst<float> c, double* red, const float* __restrict__ inflow_t) {
+                          Geom g, Phys ph, AdjConst<float> c, double* red, const float* __restrict__ inflow_t,
+                          const __grid_constant__ PlaneTab tab) {
     extern __shared__ float stage[];  // [slot][value 0..37][thread]
-    const I S = (I)g.S;
+    const long long S = g.S;
+    // element q S + off of A, Lin, Lout (off a cell index, q a constant)
+    auto pa = [&](int q, int off) -> const float* { return RLB_CHK_PTR(tab.a[q], off, S); };
+    auto pl = [&](int q, int off) -> const float* { return RLB_CHK_PTR(tab.l[q], off, S); };
+    auto po = [&](int q, int off) -> float* { return RLB_CHK_PTR(tab.o[q], off, S); };
     const int tid = threadIdx.x;
     const long long stride = (long long)gridDim.x * blockDim.x;
     const uint32_t scol = (uint32_t)__cvta_generic_to_shared(stage) + 4u * tid;
@@ -645,11 +660,9 @@ __global__ void __launch_bounds__(kStageThreads, 3)
     auto issue = [&](int cidx, const PullOffsets& o, int base, int slot) {
         const uint32_t s0 = scol + 4u * (uint32_t)(slot * 38 * kStageThreads);
 #pragma unroll
-        for (int i = 0; i < 19; ++i)
-            cp_async4(s0 + 4u * (uint32_t)(i * kStageThreads), RLB_CHK_PTR(A, (base + i) * S + cidx + o.src(i), 38ll * S));
+        for (int i = 0; i < 19; ++i) cp_async4(s0 + 4u * (uint32_t)(i * kStageThreads), pa(base + i, cidx + o.src(i)));
 #pragma unroll
-        for (int i = 0; i < 19; ++i)
-            cp_async4(s0 + 4u * (uint32_t)((19 + i) * kStageThreads), RLB_CHK_PTR(Lin, (base + i) * S + cidx, 38ll * S));
+        for (int i = 0; i < 19; ++i) cp_async4(s0 + 4u * (uint32_t)((19 + i) * kStageThreads), pl(base + i, cidx));
     };
 
     float tau_acc = 0.0f;
@@ -700,7 +713,7 @@ __global__ void __launch_bounds__(kStageThreads, 3)
                     for (int i = 1; i < 19; ++i) {
                         if (is_solid(h[i])) {
                             bounced |= 1u << i;
-                            h[i] = A[RLB_CHK((19 + opp(i)) * S + idx, 38ll * S)];
+                            h[i] = *pa(19 + opp(i), idx);
                         }
                     }
                 }
@@ -708,7 +721,7 @@ __global__ void __launch_bounds__(kStageThreads, 3)
                 for (int i = 0; i < 19; ++i) mug[i] = sval(sg, 19 + i);
                 if (dup) {
 #pragma unroll
-                    for (int i = 0; i < 19; ++i) mug[i] += Lin[RLB_CHK((19 + i) * S + idx + dup, 38ll * S)];
+                    for (int i = 0; i < 19; ++i) mug[i] += *pl(19 + i, idx + dup);
                 }
                 cell_g(h, mug, c, r);
             }
@@ -722,8 +735,8 @@ __global__ void __launch_bounds__(kStageThreads, 3)
         } else if (solid) {  // never updated: identity
 #pragma unroll
             for (int i = 0; i < 19; ++i) {
-                Lout[RLB_CHK(i * S + idx, 38ll * S)] = sval(sf, 19 + i);
-                Lout[RLB_CHK((19 + i) * S + idx, 38ll * S)] = sval(sg, 19 + i);
+                *po(i, idx) = sval(sf, 19 + i);
+                *po(19 + i, idx) = sval(sg, 19 + i);
             }
         } else {
             float h[19], muf[19];
@@ -732,13 +745,13 @@ __global__ void __launch_bounds__(kStageThreads, 3)
             if (bounced) {
 #pragma unroll
                 for (int i = 1; i < 19; ++i)
-                    if ((bounced >> i) & 1u) h[i] = A[RLB_CHK(opp(i) * S + idx, 38ll * S)];
+                    if ((bounced >> i) & 1u) h[i] = *pa(opp(i), idx);
             }
 #pragma unroll
             for (int i = 0; i < 19; ++i) muf[i] = sval(sf, 19 + i);
             if (dup) {
 #pragma unroll
-                for (int i = 0; i < 19; ++i) muf[i] += Lin[RLB_CHK(i * S + idx + dup, 38ll * S)];
+                for (int i = 0; i < 19; ++i) muf[i] += *pl(i, idx + dup);
             }
             float tf, aS, fbx, fby, fbz;
             cell_f(h, muf, r, c, tf, aS, fbx, fby, fbz);
@@ -748,9 +761,9 @@ __global__ void __launch_bounds__(kStageThreads, 3)
                                     r.bz, r.mx, r.my, r.mz, vE, vx, vy, vz);
             scatter_cell(muf, mug, aS, vE, vx, vy, vz, c, [&](int q, int i, float v) {
                 if ((bounced >> i) & 1u)
-                    Lout[RLB_CHK((q - i + opp(i)) * S + idx, 38ll * S)] = v;
+                    *po(q - i + opp(i), idx) = v;
                 else
-                    Lout[RLB_CHK(q * S + idx + o.src(i), 38ll * S)] = v;
+                    *po(q, idx + o.src(i)) = v;
             });
             zero_to_ghost<float, XBC>(x, g.nx, idx, S, Lout);
         }
@@ -930,11 +943,16 @@ static int adjoint_step_t(const Geom& g, const Phys& ph, const T* A, const T* Li
     int warps = 0;
     if constexpr (sizeof(T) == 4) {
         if (g.adj_pipe == 2) {
-            const bool idx32 = !g.adj_idx64 && 38 * g.S < (1ll << 31);
+            PlaneTab tab;
+            for (int q = 0; q < 38; ++q) {
+                tab.a[q] = (const float*)A + (long long)q * g.S;
+                tab.l[q] = (const float*)Li + (long long)q * g.S;
+                tab.o[q] = (float*)Lo + (long long)q * g.S;
+            }
             auto staged = [&](auto kern) {
                 // the shared-memory opt-in, once per device and kernel
-                static unsigned char attr[64][6];
-                const int which = g.xbc + (idx32 ? 0 : 3);
+                static unsigned char attr[64][3];
+                const int which = g.xbc;
                 int dev = 0;
                 cudaGetDevice(&dev);
                 if (dev >= 0 && dev < 64 && !attr[dev][which]) {
@@ -942,20 +960,13 @@ static int adjoint_step_t(const Geom& g, const Phys& ph, const T* A, const T* Li
                     attr[dev][which] = 1;
                 }
                 const int grid = persistent_grid(3);
-                kern<<<grid, kStageThreads, kStageSmemBytes, st>>>(A, Li, Lo, g, ph, c, red, inflow_t);
+                kern<<<grid, kStageThreads, kStageSmemBytes, st>>>(A, Li, Lo, g, ph, c, red, inflow_t, tab);
                 return grid * (kStageThreads / 32);
             };
-            if (idx32) {
-                switch (g.xbc) {
-                    case XBC_PERIODIC: return staged(k_adjoint_step_staged<XBC_PERIODIC, int>);
-                    case XBC_INFLOW_OUTFLOW: return staged(k_adjoint_step_staged<XBC_INFLOW_OUTFLOW, int>);
-                    default: return staged(k_adjoint_step_staged<XBC_OUTFLOW_BOTH, int>);
-                }
-            }
             switch (g.xbc) {
-                case XBC_PERIODIC: return staged(k_adjoint_step_staged<XBC_PERIODIC, long long>);
-                case XBC_INFLOW_OUTFLOW: return staged(k_adjoint_step_staged<XBC_INFLOW_OUTFLOW, long long>);
-                default: return staged(k_adjoint_step_staged<XBC_OUTFLOW_BOTH, long long>);
+                case XBC_PERIODIC: return staged(k_adjoint_step_staged<XBC_PERIODIC>);
+                case XBC_INFLOW_OUTFLOW: return staged(k_adjoint_step_staged<XBC_INFLOW_OUTFLOW>);
+                default: return staged(k_adjoint_step_staged<XBC_OUTFLOW_BOTH>);
             }
         }
     }

@@ -39,7 +39,6 @@ struct Geom {
     int pipe_blocks;  // resident blocks per SM of the persistent variant (tuning)
     FastDiv div_nx, div_ny;
     int adj_pipe;  // FP32 adjoint kernel: 0 one cell per thread, 1 persistent, 2 staged (tuning)
-    int adj_idx64;  // 1: 64-bit element offsets in the staged adjoint even where 32 bits suffice (testing)
     int zhalo;      // 1: planes z = 0 and z = nz-1 are halo copies, not updated by a step
     int f64df;      // 1: the FP64 step computes in compensated binary32 pairs (ablation)
 };

@@ -74,7 +74,7 @@ def _adjoint_inputs(w, sim, seed):
 
 def adjoint(out):
     """Every adjoint kernel (both precisions; FP32: one cell per thread,
-    persistent, shared-memory staged with 32- and 64-bit offsets; the
+    persistent, shared-memory staged; the
     allocation-free step; macro and field adjoints); the parity of the
     adjoint step with the oracle's taped adjoint."""
     from paper_0912_2913_gb300 import RLB
@@ -85,9 +85,9 @@ def adjoint(out):
         w = tiny_workload(nx, ny, nz, xbc, seed=12, solid_cells=s)
         p = oracle.Params(**w.params())
         for prec in ("fp64", "fp32"):
-            modes = ("0", "1", "2", "2w") if prec == "fp32" else ("0",)
+            modes = ("0", "1", "2") if prec == "fp32" else ("0",)
             for mode in modes:
-                _set_env(RLB_ADJ_PIPE=mode[0], RLB_ADJ_IDX64="1" if mode == "2w" else "0")
+                _set_env(RLB_ADJ_PIPE=mode)
                 sim = RLB.from_workload(w, prec, device="cuda:0").init_fields(w.n, w.eps, w.beta, w.solid)
                 sim.step(3)
                 state = sim.state().clone()
@@ -126,7 +126,7 @@ def adjoint(out):
                                    torch.empty(shp, **f64), torch.empty((3,) + shp, **f64), torch.zeros(3, **f64))
                 sim.sync()
                 sim.close()
-    _set_env(RLB_ADJ_PIPE="2", RLB_ADJ_IDX64="0")
+    _set_env(RLB_ADJ_PIPE="2")
     out["groups"]["adjoint"] = N.rlb_debug_bounds_violations()
     out["errors"]["adjoint_fp64"] = worst["fp64"]
     out["errors"]["adjoint_fp32"] = worst["fp32"]

@@ -86,17 +86,15 @@ def test_adjoint_step_parity(case, prec):
     sim.close()
 
 
-@pytest.mark.parametrize("mode", ["0", "1", "2", "2w"])
+@pytest.mark.parametrize("mode", ["0", "1", "2"])
 @pytest.mark.parametrize("case", [CASES[2], CASES[4], dict(nx=70, ny=40, nz=33, xbc=1, solid=((30, 20, 16), (31, 20, 16)))],
                          ids=["inflow", "ragged", "multi_sweep"])
 def test_fp32_adjoint_kernels(case, mode, monkeypatch):
     """The three FP32 adjoint kernels (one cell per thread, persistent,
-    persistent shared-memory staged with 32- and 64-bit offsets; RLB_ADJ_PIPE,
-    RLB_ADJ_IDX64) against the oracle; the
+    persistent shared-memory staged; RLB_ADJ_PIPE) against the oracle; the
     last lattice (92400 cells) needs more than one sweep of the persistent
     grids over the cells."""
-    monkeypatch.setenv("RLB_ADJ_PIPE", mode[0])
-    monkeypatch.setenv("RLB_ADJ_IDX64", "1" if mode == "2w" else "0")
+    monkeypatch.setenv("RLB_ADJ_PIPE", mode)
     w, p, sim, st, gstate, rng = _setup(case, "fp32", 13)
     lam_in = rng.normal(size=st.shape).astype(np.float32).astype(np.float64)
     ref_out, ref_dtau, ref_db = oracle.adjoint_step(p, st, lam_in, w.solid)
@@ -290,8 +288,8 @@ def test_oracle_taped_gradient_shock_tube_short():
 
 @pytest.mark.slow
 def test_random_box_512_fp32_adjoint_step_against_fp64():
-    """One adjoint step on the 512^3 box (38 S > 2^31: the staged FP32 kernel
-    runs with 64-bit element offsets): the FP32 adjoint against the FP64
+    """One adjoint step on the 512^3 box (38 S > 2^31 elements per state,
+    every plane addressed from its own base): the FP32 adjoint against the FP64
     adjoint of the same run after 20 steps, with the same random lambda_{t+1},
     on the 64^3 lattice of cells x, y, z = 0 (mod 8) and in dL/dtau."""
     from paper_0912_2913_gb300 import RLB
