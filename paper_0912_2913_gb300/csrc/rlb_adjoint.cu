@@ -622,6 +622,9 @@ constexpr size_t kStageSmemBytes = sizeof(float) * kStageSlots * 38 * kStageThre
 __device__ __forceinline__ void cp_async4(uint32_t saddr, const void* gptr) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(saddr), "l"(gptr) : "memory");
 }
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void* gptr) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(gptr) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
@@ -752,6 +755,212 @@ __global__ void __launch_bounds__(kStageThreads, 3)
             if (dup) {
 #pragma unroll
                 for (int i = 0; i < 19; ++i) muf[i] += *pl(i, idx + dup);
+            }
+            float tf, aS, fbx, fby, fbz;
+            cell_f(h, muf, r, c, tf, aS, fbx, fby, fbz);
+            tau_acc += (r.tacc + tf) * c.inv_tau2_t;
+            float vE, vx, vy, vz;
+            recovery_adjoint<float>(r.ae, fbx + r.gbx, fby + r.gby, fbz + r.gbz, r.Et, r.sqt, r.Dt, r.bx, r.by,
+                                    r.bz, r.mx, r.my, r.mz, vE, vx, vy, vz);
+            scatter_cell(muf, mug, aS, vE, vx, vy, vz, c, [&](int q, int i, float v) {
+                if ((bounced >> i) & 1u)
+                    *po(q - i + opp(i), idx) = v;
+                else
+                    *po(q, idx + o.src(i)) = v;
+            });
+            zero_to_ghost<float, XBC>(x, g.nx, idx, S, Lout);
+        }
+        sg = sn;
+        x = xn;
+        o = on;
+    }
+    cp_async_wait<0>();
+    warp_partials<float>((double)tau_acc, bin0, bin1, bin2, has_b, red);
+}
+
+// Cooperative form of the staged kernel (the default FP32 adjoint kernel).
+// The pulled populations are staged per thread as above; lambda_t+1, read at
+// the cell's own index, is copied by the whole block in 16-byte chunks (a
+// quarter of the copy instructions), so the block meets at two barriers per
+// cell: after the G phase has landed (then every thread is past the f phase
+// of the previous cell, and its slots can be refilled) and after the F phase
+// has landed.  Because every cell's lambda_t+1 is in the ring, the ghost
+// planes and the outflow-copy cells read theirs from it instead of from HBM
+// (a lane that waits on HBM would hold the whole block at the next barrier).
+template <int XBC>
+__global__ void __launch_bounds__(kStageThreads, 3)
+    k_adjoint_step_coop(const float* __restrict__ A, const float* __restrict__ Lin, float* __restrict__ Lout,
+                          Geom g, Phys ph, AdjConst<float> c, double* red, const float* __restrict__ inflow_t,
+                          const __grid_constant__ PlaneTab tab) {
+    extern __shared__ float stage[];  // [slot][value 0..37][thread]
+    const long long S = g.S;
+    // element q S + off of A, Lin, Lout (off a cell index, q a constant)
+    auto pa = [&](int q, int off) -> const float* { return RLB_CHK_PTR(tab.a[q], off, S); };
+    auto pl = [&](int q, int off) -> const float* { return RLB_CHK_PTR(tab.l[q], off, S); };
+    auto po = [&](int q, int off) -> float* { return RLB_CHK_PTR(tab.o[q], off, S); };
+    const int tid = threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const uint32_t scol = (uint32_t)__cvta_generic_to_shared(stage) + 4u * tid;
+    auto sval = [&](int slot, int q) -> float { return stage[(slot * 38 + q) * kStageThreads + tid]; };
+    // another thread's column (lambda_t+1 of every cell of the block is staged)
+    auto sval_c = [&](int slot, int q, int col) -> float { return stage[(slot * 38 + q) * kStageThreads + col]; };
+    auto is_ghost = [&](int x) { return XBC != XBC_PERIODIC && (x == 0 || x == g.nx - 1); };
+    // the pulled values of one phase (base 19: g, base 0: f) of this thread's
+    // cell (pull offsets o) into its column of a slot
+    auto issue = [&](int cidx, const PullOffsets& o, int base, int slot) {
+        const uint32_t s0 = scol + 4u * (uint32_t)(slot * 38 * kStageThreads);
+#pragma unroll
+        for (int i = 0; i < 19; ++i) cp_async4(s0 + 4u * (uint32_t)(i * kStageThreads), pa(base + i, cidx + o.src(i)));
+    };
+    // lambda_t+1 of one phase for the block's cells [cb, cb + 128): warp w
+    // copies planes w, w + 4, ..., lane l the 16 bytes of cells cb + 4l .. + 3
+    // (S is a multiple of 4: a chunk lies wholly inside or outside a plane)
+    const int wq = tid >> 5, lane4 = 4 * (tid & 31);
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(stage);
+    auto issue_lam = [&](long long cb, int base, int slot) {
+        const long long cell = cb + lane4;
+        if (cell >= S) return;
+        const uint32_t s0 = sbase + 4u * (uint32_t)((slot * 38 + 19) * kStageThreads + lane4);
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            const int q = wq + 4 * m;
+            if (q < 19) cp_async16(s0 + 4u * (uint32_t)(q * kStageThreads), RLB_CHK_PTR(Lin, (long long)(base + q) * S + cell, 38ll * S));
+        }
+    };
+
+    float tau_acc = 0.0f;
+    double bin0 = 0.0, bin1 = 0.0, bin2 = 0.0;
+    bool has_b = false;
+    // block-uniform loop over the block's cells [cb, cb + 128) (every thread
+    // reaches every barrier); 64-bit: cb + stride cannot wrap
+    long long cb = (long long)blockIdx.x * blockDim.x;
+    long long li = cb + tid;
+    int idx = li < g.N ? (int)li : 0;
+    int x = 0, y = 0, z = 0;
+    PullOffsets o{};
+    if (li < g.N) {
+        cell_coords(g, idx, x, y, z);
+        o = PullOffsets(g, x, y, z);
+        if (!is_ghost(x)) issue(idx, o, 19, 0);
+    }
+    if (cb < g.N) issue_lam(cb, 19, 0);
+    cp_async_commit();
+    int sg = 0;
+    for (; cb < g.N; cb += stride) {
+        li = cb + tid;
+        const bool act = li < g.N;
+        idx = act ? (int)li : 0;
+        const int sf = sg == kStageSlots - 1 ? 0 : sg + 1;
+        const int sn = sf == kStageSlots - 1 ? 0 : sf + 1;
+        const bool ghost = !act || is_ghost(x);
+        // the inflow ghost's own f_0 (solid marker), loaded early
+        const float own0 = (XBC == XBC_INFLOW_OUTFLOW && act && x == 0) ? *pa(0, idx) : 0.0f;
+        const long long nl = li + stride;
+        const int nidx = nl < g.N ? (int)nl : 0;
+        int xn = 0, yn = 0, zn = 0;
+        PullOffsets on{};
+        if (nl < g.N) {
+            cell_coords(g, nidx, xn, yn, zn);
+            on = PullOffsets(g, xn, yn, zn);
+        }
+        cp_async_wait<0>();  // G_k has landed (this thread's copies)
+        __syncthreads();     // ... and every thread's; all are past f phase k-1
+        if (!ghost) issue(idx, o, 0, sf);
+        issue_lam(cb, 0, sf);
+        cp_async_commit();
+        // ---- g phase
+        unsigned bounced = 0u;
+        bool solid = false;
+        const int dup = dup_of<XBC>(x, g.nx);
+        const int dcol = tid + dup;  // the copying ghost's column, when in this block
+        const bool dup_in = dcol >= 0 && dcol < kStageThreads;
+        float mug[19];
+        CellG<float> r;
+        if (!ghost) {
+            float h[19];
+#pragma unroll
+            for (int i = 0; i < 19; ++i) h[i] = sval(sg, i);
+            solid = is_solid(h[0]);  // the cell's own g_0 (pull offset 0)
+            if (!solid) {
+                if (isnan(sum19(h))) {
+#pragma unroll
+                    for (int i = 1; i < 19; ++i) {
+                        if (is_solid(h[i])) {
+                            bounced |= 1u << i;
+                            h[i] = *pa(19 + opp(i), idx);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 19; ++i) mug[i] = sval(sg, 19 + i);
+                if (dup) {
+                    if (dup_in) {
+#pragma unroll
+                        for (int i = 0; i < 19; ++i) mug[i] += sval_c(sg, 19 + i, dcol);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 19; ++i) mug[i] += *pl(19 + i, idx + dup);
+                    }
+                }
+                cell_g(h, mug, c, r);
+            }
+        }
+        if (nl < g.N && !is_ghost(xn)) issue(nidx, on, 19, sn);
+        if (cb + stride < g.N) issue_lam(cb + stride, 19, sn);
+        cp_async_commit();
+        cp_async_wait<1>();  // F_k has landed (this thread's copies)
+        __syncthreads();     // ... and every thread's
+        // ---- f phase, scatter
+        if (!act) {
+        } else if (ghost) {
+            // ghost_cell with lambda_t+1 from the ring
+            const int inward = (x == 0) ? 1 : -1;
+#pragma unroll
+            for (int i = 0; i < 19; ++i) {
+                if (vel_x(i) != inward) {
+                    *po(i, idx) = 0.0f;
+                    *po(19 + i, idx) = 0.0f;
+                }
+            }
+            if (XBC == XBC_INFLOW_OUTFLOW && x == 0 && !is_solid(own0)) {
+                float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
+#pragma unroll
+                for (int q = 0; q < 38; ++q) {
+                    const float l = q < 19 ? sval(sf, 19 + q) : sval(sg, q);
+                    a0 += l * inflow_t[3 * q + 0];
+                    a1 += l * inflow_t[3 * q + 1];
+                    a2 += l * inflow_t[3 * q + 2];
+                }
+                bin0 += (double)a0;
+                bin1 += (double)a1;
+                bin2 += (double)a2;
+                has_b = true;
+            }
+        } else if (solid) {  // never updated: identity
+#pragma unroll
+            for (int i = 0; i < 19; ++i) {
+                *po(i, idx) = sval(sf, 19 + i);
+                *po(19 + i, idx) = sval(sg, 19 + i);
+            }
+        } else {
+            float h[19], muf[19];
+#pragma unroll
+            for (int i = 0; i < 19; ++i) h[i] = sval(sf, i);
+            if (bounced) {
+#pragma unroll
+                for (int i = 1; i < 19; ++i)
+                    if ((bounced >> i) & 1u) h[i] = *pa(opp(i), idx);
+            }
+#pragma unroll
+            for (int i = 0; i < 19; ++i) muf[i] = sval(sf, 19 + i);
+            if (dup) {
+                if (dup_in) {
+#pragma unroll
+                    for (int i = 0; i < 19; ++i) muf[i] += sval_c(sf, 19 + i, dcol);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 19; ++i) muf[i] += *pl(i, idx + dup);
+                }
             }
             float tf, aS, fbx, fby, fbz;
             cell_f(h, muf, r, c, tf, aS, fbx, fby, fbz);
@@ -943,6 +1152,7 @@ static int adjoint_step_t(const Geom& g, const Phys& ph, const T* A, const T* Li
     int warps = 0;
     if constexpr (sizeof(T) == 4) {
         if (g.adj_pipe == 2) {
+            const int coop = g.adj_coop;
             PlaneTab tab;
             for (int q = 0; q < 38; ++q) {
                 tab.a[q] = (const float*)A + (long long)q * g.S;
@@ -951,8 +1161,8 @@ static int adjoint_step_t(const Geom& g, const Phys& ph, const T* A, const T* Li
             }
             auto staged = [&](auto kern) {
                 // the shared-memory opt-in, once per device and kernel
-                static unsigned char attr[64][3];
-                const int which = g.xbc;
+                static unsigned char attr[64][6];
+                const int which = g.xbc + 3 * coop;
                 int dev = 0;
                 cudaGetDevice(&dev);
                 if (dev >= 0 && dev < 64 && !attr[dev][which]) {
@@ -963,6 +1173,14 @@ static int adjoint_step_t(const Geom& g, const Phys& ph, const T* A, const T* Li
                 kern<<<grid, kStageThreads, kStageSmemBytes, st>>>(A, Li, Lo, g, ph, c, red, inflow_t, tab);
                 return grid * (kStageThreads / 32);
             };
+            // 16-byte copies of lambda_t+1: the buffer must be 16-byte aligned
+            if (coop && ((uintptr_t)Li & 15u) == 0) {
+                switch (g.xbc) {
+                    case XBC_PERIODIC: return staged(k_adjoint_step_coop<XBC_PERIODIC>);
+                    case XBC_INFLOW_OUTFLOW: return staged(k_adjoint_step_coop<XBC_INFLOW_OUTFLOW>);
+                    default: return staged(k_adjoint_step_coop<XBC_OUTFLOW_BOTH>);
+                }
+            }
             switch (g.xbc) {
                 case XBC_PERIODIC: return staged(k_adjoint_step_staged<XBC_PERIODIC>);
                 case XBC_INFLOW_OUTFLOW: return staged(k_adjoint_step_staged<XBC_INFLOW_OUTFLOW>);

@@ -225,13 +225,16 @@ rlb_status rlb_create(const rlb_params* p, void* stream, void* workspace, size_t
         // Tuning knobs (no effect on results beyond rounding): RLB_TMA=1
         // selects the TMA-staged FP32 step, RLB_F32_VARIANT the launch variant
         // of the plain one, RLB_ADJ_PIPE the FP32 adjoint kernel (0: one cell
-        // per thread, 1: persistent, 2: persistent shared-memory staged).
+        // per thread, 1: persistent, 2: persistent shared-memory staged;
+        // RLB_ADJ_COOP=0 stages lambda per thread instead of per block).
         const char* t = getenv("RLB_TMA");
         g.tma = (t && t[0] == '1' && !g.zhalo) ? 1 : 0;  // the TMA-staged step updates every z plane
         const char* v = getenv("RLB_F32_VARIANT");
         g.variant = v ? atoi(v) : -1;  // -1: chosen by timing at the first step
         const char* ap = getenv("RLB_ADJ_PIPE");
         g.adj_pipe = ap ? atoi(ap) : 2;
+        const char* ac = getenv("RLB_ADJ_COOP");
+        g.adj_coop = (ac && ac[0] == '0') ? 0 : 1;
         const char* pb = getenv("RLB_PIPE_BLOCKS");
         g.pipe_blocks = pb ? atoi(pb) : 3;
         // RLB_F64_ARITH=df: the FP64 step with its arithmetic in compensated

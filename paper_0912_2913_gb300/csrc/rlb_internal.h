@@ -38,7 +38,8 @@ struct Geom {
     int variant; // launch variant of the one-cell-per-thread FP32 step (tuning)
     int pipe_blocks;  // resident blocks per SM of the persistent variant (tuning)
     FastDiv div_nx, div_ny;
-    int adj_pipe;  // FP32 adjoint kernel: 0 one cell per thread, 1 persistent, 2 staged (tuning)
+    int adj_pipe;   // FP32 adjoint kernel: 0 one cell per thread, 1 persistent, 2 staged (tuning)
+    int adj_coop;   // staged FP32 adjoint: 1 lambda copied by the whole block (default), 0 per thread
     int zhalo;      // 1: planes z = 0 and z = nz-1 are halo copies, not updated by a step
     int f64df;      // 1: the FP64 step computes in compensated binary32 pairs (ablation)
 };

@@ -74,7 +74,8 @@ def _adjoint_inputs(w, sim, seed):
 
 def adjoint(out):
     """Every adjoint kernel (both precisions; FP32: one cell per thread,
-    persistent, shared-memory staged; the
+    persistent, shared-memory staged with lambda copied by the block or per
+    thread; the
     allocation-free step; macro and field adjoints); the parity of the
     adjoint step with the oracle's taped adjoint."""
     from paper_0912_2913_gb300 import RLB
@@ -85,9 +86,9 @@ def adjoint(out):
         w = tiny_workload(nx, ny, nz, xbc, seed=12, solid_cells=s)
         p = oracle.Params(**w.params())
         for prec in ("fp64", "fp32"):
-            modes = ("0", "1", "2") if prec == "fp32" else ("0",)
+            modes = ("0", "1", "2", "2p") if prec == "fp32" else ("0",)
             for mode in modes:
-                _set_env(RLB_ADJ_PIPE=mode)
+                _set_env(RLB_ADJ_PIPE=mode[0], RLB_ADJ_COOP="0" if mode == "2p" else "1")
                 sim = RLB.from_workload(w, prec, device="cuda:0").init_fields(w.n, w.eps, w.beta, w.solid)
                 sim.step(3)
                 state = sim.state().clone()
@@ -126,7 +127,7 @@ def adjoint(out):
                                    torch.empty(shp, **f64), torch.empty((3,) + shp, **f64), torch.zeros(3, **f64))
                 sim.sync()
                 sim.close()
-    _set_env(RLB_ADJ_PIPE="2")
+    _set_env(RLB_ADJ_PIPE="2", RLB_ADJ_COOP="1")
     out["groups"]["adjoint"] = N.rlb_debug_bounds_violations()
     out["errors"]["adjoint_fp64"] = worst["fp64"]
     out["errors"]["adjoint_fp32"] = worst["fp32"]

@@ -86,15 +86,22 @@ def test_adjoint_step_parity(case, prec):
     sim.close()
 
 
-@pytest.mark.parametrize("mode", ["0", "1", "2"])
-@pytest.mark.parametrize("case", [CASES[2], CASES[4], dict(nx=70, ny=40, nz=33, xbc=1, solid=((30, 20, 16), (31, 20, 16)))],
-                         ids=["inflow", "ragged", "multi_sweep"])
+@pytest.mark.parametrize("mode", ["0", "1", "2", "2p"])
+@pytest.mark.parametrize("case", [CASES[2], CASES[4], dict(nx=70, ny=40, nz=33, xbc=1, solid=((30, 20, 16), (31, 20, 16))),
+                                  dict(nx=37, ny=9, nz=11, xbc=2, solid=((12, 4, 2),))],
+                         ids=["inflow", "ragged", "multi_sweep", "outflow2_edges"])
 def test_fp32_adjoint_kernels(case, mode, monkeypatch):
-    """The three FP32 adjoint kernels (one cell per thread, persistent,
-    persistent shared-memory staged; RLB_ADJ_PIPE) against the oracle; the
-    last lattice (92400 cells) needs more than one sweep of the persistent
-    grids over the cells."""
-    monkeypatch.setenv("RLB_ADJ_PIPE", mode)
+    """The FP32 adjoint kernels (one cell per thread, persistent, persistent
+    shared-memory staged with lambda copied by the block or per thread;
+    RLB_ADJ_PIPE, RLB_ADJ_COOP) against the oracle; the
+    multi-sweep lattice (92400 cells) needs more than one sweep of the
+    persistent grids over the cells.  In the ragged lattice the outflow-copy
+    cell of row 44 is the last cell of a 128-cell block, and in the outflow2
+    edges lattice the x = 1 copy cell of row 83 the first one, so their
+    ghost's lambda lies in the next / previous block (read from HBM by the
+    block-copy kernel instead of from its ring)."""
+    monkeypatch.setenv("RLB_ADJ_PIPE", mode[0])
+    monkeypatch.setenv("RLB_ADJ_COOP", "0" if mode == "2p" else "1")
     w, p, sim, st, gstate, rng = _setup(case, "fp32", 13)
     lam_in = rng.normal(size=st.shape).astype(np.float32).astype(np.float64)
     ref_out, ref_dtau, ref_db = oracle.adjoint_step(p, st, lam_in, w.solid)
@@ -108,6 +115,33 @@ def test_fp32_adjoint_kernels(case, mode, monkeypatch):
     a = acc.cpu().numpy()
     assert abs(a[0] - ref_dtau) <= TOL["fp32"] * max(abs(ref_dtau), 1e-12) * 10
     assert np.max(np.abs(a[1:] - ref_db)) <= TOL["fp32"] * max(np.max(np.abs(ref_db)), 1e-12) * 10
+    sim.close()
+
+
+@pytest.mark.parametrize("case", [CASES[2], CASES[4]], ids=["inflow", "ragged"])
+def test_fp32_adjoint_unaligned_lambda(case):
+    """A lambda_{t+1} buffer that is not 16-byte aligned (a view 4 bytes into
+    a larger allocation) cannot take the block's 16-byte copies: the step
+    runs the per-thread staged kernel, whose results equal the default
+    kernel's bit for bit."""
+    w, p, sim, st, gstate, rng = _setup(case, "fp32", 17)
+    lam_in = rng.normal(size=st.shape)
+    li = sim.cells_to_state(torch.from_numpy(lam_in).cuda())
+    buf = torch.empty(li.numel() + 1, dtype=li.dtype, device=li.device)
+    li_odd = buf[1:].view(li.shape)
+    li_odd.copy_(li)
+    assert li_odd.data_ptr() % 16 != 0
+    outs = []
+    for lam in (li, li_odd):
+        lo = torch.full_like(li, float("nan"))
+        acc = torch.zeros(4, dtype=torch.float64, device="cuda")
+        sim.adjoint_step(gstate, lam, lo, acc[0:1], acc[1:4])
+        outs.append((lo, acc))
+    sim.sync()
+    (lo_a, acc_a), (lo_b, acc_b) = outs
+    n = sim.N
+    assert torch.equal(lo_a[:, :n].view(torch.int32), lo_b[:, :n].view(torch.int32))
+    assert torch.equal(acc_a, acc_b)
     sim.close()
 
 
