@@ -814,14 +814,15 @@ def run_reference(args):
 def run_profile(args):
     """Short runs of the benchmark workload for ncu captures: --profile step
     runs warm-up + --steps forward steps; --profile adjoint runs --steps
-    (forward recompute + adjoint) steps; --profile box runs forward steps of
-    the periodic random box of side --box."""
+    (forward recompute + adjoint) steps; --profile box / adjoint_box run
+    forward / adjoint steps on the periodic random box of side --box."""
     import torch
 
     import workloads as W
     from paper_0912_2913_gb300 import RLB
 
-    w = W.random_box(L=args.box, steps=args.steps) if args.profile == "box" else W.sphere_3d(steps=args.steps)
+    on_box = args.profile in ("box", "adjoint_box")
+    w = W.random_box(L=args.box, steps=args.steps) if on_box else W.sphere_3d(steps=args.steps)
     sim = RLB.from_workload(w, args.precision, device="cuda:0").init_fields(w.n, w.eps, w.beta, w.solid)
     if args.profile in ("step", "box"):
         sim.step(args.steps)
@@ -850,7 +851,7 @@ def main(argv=None):
     ap.add_argument("--grad-steps", type=int, default=2000,
                     help="steps of the whole-gradient leg (rlb_run forward + backward); 0 skips it")
     ap.add_argument("--workload", choices=["box512", "sphere"], default="box512")
-    ap.add_argument("--profile", choices=["step", "adjoint", "box"], default=None,
+    ap.add_argument("--profile", choices=["step", "adjoint", "box", "adjoint_box"], default=None,
                     help="short run of one kernel family for ncu captures (no JSON bench line)")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--box", type=int, default=256)

@@ -829,6 +829,7 @@ __global__ void __launch_bounds__(kStageThreads, 3)
     };
 
     float tau_acc = 0.0f;
+    float ga0 = 0.0f, ga1 = 0.0f, ga2 = 0.0f;  // this lane's share of the inflow plane's terms
     double bin0 = 0.0, bin1 = 0.0, bin2 = 0.0;
     bool has_b = false;
     // block-uniform loop over the block's cells [cb, cb + 128) (every thread
@@ -922,20 +923,7 @@ __global__ void __launch_bounds__(kStageThreads, 3)
                     *po(19 + i, idx) = 0.0f;
                 }
             }
-            if (XBC == XBC_INFLOW_OUTFLOW && x == 0 && !is_solid(own0)) {
-                float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
-#pragma unroll
-                for (int q = 0; q < 38; ++q) {
-                    const float l = q < 19 ? sval(sf, 19 + q) : sval(sg, q);
-                    a0 += l * inflow_t[3 * q + 0];
-                    a1 += l * inflow_t[3 * q + 1];
-                    a2 += l * inflow_t[3 * q + 2];
-                }
-                bin0 += (double)a0;
-                bin1 += (double)a1;
-                bin2 += (double)a2;
-                has_b = true;
-            }
+            // (the inflow plane's dL/dbeta_in terms: below, by the whole warp)
         } else if (solid) {  // never updated: identity
 #pragma unroll
             for (int i = 0; i < 19; ++i) {
@@ -976,11 +964,37 @@ __global__ void __launch_bounds__(kStageThreads, 3)
             });
             zero_to_ghost<float, XBC>(x, g.nx, idx, S, Lout);
         }
+        if constexpr (XBC == XBC_INFLOW_OUTFLOW) {
+            // dL/dbeta_in = lambda_t+1 . d eq_in / d beta_in at each fluid
+            // inflow ghost: its 38 terms spread over the warp (lane l takes
+            // q = l and l + 32) from the ghost's column of the ring, each lane
+            // adding into its own partial sums (summed over the warp at the end)
+            unsigned m = __ballot_sync(0xffffffffu, act && x == 0 && !is_solid(own0));
+            const int lane = tid & 31;
+            while (m) {
+                const int col = (tid & ~31) + __ffs(m) - 1;
+                m &= m - 1;
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const int q = lane + 32 * r;
+                    if (q < 38) {
+                        const float l = q < 19 ? sval_c(sf, 19 + q, col) : sval_c(sg, q, col);
+                        ga0 = fmaf(l, inflow_t[3 * q + 0], ga0);
+                        ga1 = fmaf(l, inflow_t[3 * q + 1], ga1);
+                        ga2 = fmaf(l, inflow_t[3 * q + 2], ga2);
+                    }
+                }
+                has_b = true;
+            }
+        }
         sg = sn;
         x = xn;
         o = on;
     }
     cp_async_wait<0>();
+    bin0 += (double)ga0;
+    bin1 += (double)ga1;
+    bin2 += (double)ga2;
     warp_partials<float>((double)tau_acc, bin0, bin1, bin2, has_b, red);
 }
 

@@ -122,8 +122,9 @@ def test_fp32_adjoint_kernels(case, mode, monkeypatch):
 def test_fp32_adjoint_unaligned_lambda(case):
     """A lambda_{t+1} buffer that is not 16-byte aligned (a view 4 bytes into
     a larger allocation) cannot take the block's 16-byte copies: the step
-    runs the per-thread staged kernel, whose results equal the default
-    kernel's bit for bit."""
+    runs the per-thread staged kernel, whose lambda_t and dL/dtau equal the
+    default kernel's bit for bit (dL/dbeta_in: another summation order, the
+    default kernel spreading the inflow plane's terms over the warp)."""
     w, p, sim, st, gstate, rng = _setup(case, "fp32", 17)
     lam_in = rng.normal(size=st.shape)
     li = sim.cells_to_state(torch.from_numpy(lam_in).cuda())
@@ -141,7 +142,10 @@ def test_fp32_adjoint_unaligned_lambda(case):
     (lo_a, acc_a), (lo_b, acc_b) = outs
     n = sim.N
     assert torch.equal(lo_a[:, :n].view(torch.int32), lo_b[:, :n].view(torch.int32))
-    assert torch.equal(acc_a, acc_b)
+    assert torch.equal(acc_a[0], acc_b[0])
+    scale = float(acc_a[1:].abs().max())
+    assert scale > 0.0  # the inflow plane contributes
+    assert float((acc_a[1:] - acc_b[1:]).abs().max()) <= 1e-5 * scale
     sim.close()
 
 
