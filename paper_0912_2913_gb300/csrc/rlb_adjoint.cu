@@ -243,6 +243,12 @@ template <typename T>
 struct AdjConst {
     T om, omw, c_l, inv_cl, inv_cl2, n_ref, g0a, g0b, eps_ref_t, inv_tau2_t;
     double inv_tau2;
+    // per-run products for the binary64 cell functions (cell_g64 and after);
+    // the _36 ones divided by 36, for the pair sums carried times 36
+    double c2, c2p1;                  // 2/c_l^2, 2/c_l^2 + 1
+    double i2_36, c2_36, c3_36, c4_36, c6_36, c12_36;  // 1/c_l^2, 2/c_l^2, 3/c_l, 4/c_l, 6/c_l^2, 12/c_l^2
+    double three_cl, m3cl2, om_cl;    // 3 c_l, -3 c_l^2, omega c_l
+    double g0_eg, g0_e, g0_egb2;      // g_0^eq = eg g0_eg + eps g0_e + eg b2 g0_egb2
 };
 
 template <typename T>
@@ -259,6 +265,20 @@ static AdjConst<T> make_adj_const(const Phys& ph) {
     c.eps_ref_t = (T)ph.eps_ref;
     c.inv_tau2 = ph.omega * ph.omega;
     c.inv_tau2_t = (T)c.inv_tau2;
+    c.c2 = 2.0 * ph.inv_cl2;
+    c.i2_36 = ph.inv_cl2 / 36.0;
+    c.c2_36 = 2.0 * ph.inv_cl2 / 36.0;
+    c.c3_36 = 3.0 * ph.inv_cl / 36.0;
+    c.c4_36 = 4.0 * ph.inv_cl / 36.0;
+    c.c6_36 = 6.0 * ph.inv_cl2 / 36.0;
+    c.c12_36 = 12.0 * ph.inv_cl2 / 36.0;
+    c.three_cl = 3.0 * ph.c_l;
+    c.m3cl2 = -3.0 * ph.c_l * ph.c_l;
+    c.om_cl = ph.omega * ph.c_l;
+    c.g0_eg = 4.0 * kW0;
+    c.g0_e = -kW0 * (2.0 * ph.inv_cl2 + 1.0);
+    c.g0_egb2 = -2.0 * kW0 * ph.inv_cl2;
+    c.c2p1 = 2.0 * ph.inv_cl2 + 1.0;
     return c;
 }
 
@@ -289,8 +309,9 @@ __device__ __forceinline__ T dot19(const T* a, const T* b) {
 // What the g phase leaves for the f phase and the recovery adjoint.
 template <typename T>
 struct CellG {
-    T mx, my, mz, Et, sqt, Dt, bx, by, bz;  // moments, recovery
+    T mx, my, mz, Et, sqt, Dt, bx, by, bz;  // moments (cell_g64: M / c_l), recovery
     T tacc, ae, gbx, gby, gbz;              // sum mu_g (h - eq), d/d eps, d/d beta
+    T rD, rs;                               // 1/D, 1/s (cell_g64)
 };
 
 // Moments and recovery from the 19 g populations h, then the g part of the
@@ -451,6 +472,167 @@ __device__ __forceinline__ void scatter_cell(const T* muf, const T* mug, T aS, T
     }
 }
 
+// ---------------------------------------------------------------------------
+// The same per-cell mathematics in binary64 with fewer FP64 instructions
+// (the FP64 pipe bounds the FP64 adjoint):
+//  * the square root and the reciprocals 1/D, 1/(1 - b2), 1/s from binary32
+//    seeds and two Newton steps each (the forward step's recovery), 1/D and
+//    1/s computed once for the recovery and its adjoint;
+//  * the per-run products of 1/c_l, the weights and omega folded (AdjConst);
+//    the weighted pair sums are carried times 36 (weights 2 and 1), the
+//    1/36 folded into their coefficients;
+//  * the pair sums that depend on beta formed from beta-free moments of mu:
+//    with q_p = e_p . beta,
+//      Sdq = sum w delta_p q_p = beta . Vd,     Vd = sum w delta_p e_p,
+//      Vq  = sum w sigma_p q_p e_p = T beta,    T  = sum w sigma_p e_p e_p^T,
+//      Sq2 = sum w sigma_p q_p^2 = beta . Vq.
+// ---------------------------------------------------------------------------
+
+// x = 1/a from a binary32 seed and two Newton steps
+__device__ __forceinline__ double rcp_newton(double a) {
+    double x = rcp_seed(a);
+    x = fma(x, fma(-a, x, 1.0), x);
+    return fma(x, fma(-a, x, 1.0), x);
+}
+
+// 36 sum w s_p (36 w = 2 for the axis pairs, 1 for the diagonal ones)
+__device__ __forceinline__ double wsum9(const double* s) {
+    return fma(2.0, (s[0] + s[1]) + s[2], ((s[3] + s[4]) + (s[5] + s[6])) + (s[7] + s[8]));
+}
+// 36 sum w d_p e_p (three components)
+__device__ __forceinline__ void wvec9(const double* d, double& vx, double& vy, double& vz) {
+    vx = fma(2.0, d[0], (d[3] + d[4]) + (d[5] + d[6]));
+    vy = fma(2.0, d[1], (d[3] - d[4]) + (d[7] + d[8]));
+    vz = fma(2.0, d[2], (d[5] - d[6]) + (d[7] - d[8]));
+}
+
+__device__ __forceinline__ void cell_g64(const double* h, const double* mug, const AdjConst<double>& c,
+                                         CellG<double>& r) {
+    const double E = sum19(h);
+    double dd[9];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) dd[p] = h[2 * p + 1] - h[2 * p + 2];
+    double dx, dy, dz;  // M / c_l
+    dx = dd[0] + dd[3] + dd[4] + dd[5] + dd[6];
+    dy = dd[1] + dd[3] - dd[4] + dd[7] + dd[8];
+    dz = dd[2] + dd[5] - dd[6] + dd[7] - dd[8];
+    const double m2 = fma(dx, dx, fma(dy, dy, dz * dz));
+    const double disc = fma(4.0 * E, E, c.m3cl2 * m2);  // 4 E^2 - 3 M^2
+    double ys, hs;
+    rsqrt_seed(disc, ys, hs);
+    double sq = disc * ys;
+    sq = fma(fma(-sq, sq, disc), hs, sq);
+    sq = fma(fma(-sq, sq, disc), hs, sq);
+    const double eps = sq - E;
+    const double D = fma(3.0, E, eps);
+    const double rD = rcp_newton(D);
+    const double r3 = c.three_cl * rD;  // beta = 3 M / D
+    const double bx = dx * r3, by = dy * r3, bz = dz * r3;
+    const double b2 = (r3 * r3) * m2;
+    const double gam2 = rcp_newton(1.0 - b2);
+    // beta-free moments of mu_g (all times 36)
+    double sg[9], dg[9];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        sg[p] = mug[2 * p + 1] + mug[2 * p + 2];
+        dg[p] = mug[2 * p + 1] - mug[2 * p + 2];
+    }
+    const double s34 = sg[3] + sg[4], s56 = sg[5] + sg[6], s78 = sg[7] + sg[8];
+    const double S1 = fma(2.0, (sg[0] + sg[1]) + sg[2], (s34 + s56) + s78);
+    const double Txx = fma(2.0, sg[0], s34 + s56);
+    const double Tyy = fma(2.0, sg[1], s34 + s78);
+    const double Tzz = fma(2.0, sg[2], s56 + s78);
+    const double Txy = sg[3] - sg[4], Txz = sg[5] - sg[6], Tyz = sg[7] - sg[8];
+    double Vdx, Vdy, Vdz;
+    wvec9(dg, Vdx, Vdy, Vdz);
+    const double Vqx = fma(Txx, bx, fma(Txy, by, Txz * bz));
+    const double Vqy = fma(Txy, bx, fma(Tyy, by, Tyz * bz));
+    const double Vqz = fma(Txz, bx, fma(Tyz, by, Tzz * bz));
+    const double Sq2 = fma(Vqx, bx, fma(Vqy, by, Vqz * bz));
+    const double Sdq = fma(Vdx, bx, fma(Vdy, by, Vdz * bz));
+    // the coefficients (Eqs. equil2as/equil2bs and their derivatives), the
+    // 1/36 of the sums folded into them
+    const double eg = eps * gam2, egb2 = eg * b2;
+    const double m0 = mug[0], w0m0 = kW0 * m0;
+    const double k1 = fma(-2.0, egb2, eps) * c.i2_36, k2 = eg * c.c6_36, k3 = eg * c.c4_36;
+    const double geq0 = fma(eg, c.g0_eg, fma(eps, c.g0_e, egb2 * c.g0_egb2));
+    r.tacc = dot19(mug, h) - fma(m0, geq0, fma(k1, S1, fma(k2, Sq2, k3 * Sdq)));
+    const double SA = fma(c.c6_36, Sq2, fma(-c.c2_36 * b2, S1, c.c4_36 * Sdq));  // SYM + ASY
+    const double t4 = fma(-c.c2, b2, 4.0);                                          // 4 - 2 b2 / c_l^2
+    r.ae = fma(c.i2_36, S1, fma(gam2, SA, w0m0 * fma(gam2, t4, -c.c2p1)));
+    const double gg2 = fma(w0m0, t4, SA);
+    const double gb2 = -(c.c2 * gam2) * fma(S1, 1.0 / 36.0, w0m0);
+    const double rad = (2.0 * eps) * fma(gam2 * gam2, gg2, gb2);
+    const double cq = eg * c.c12_36;  // the Vd coefficient is k3
+    r.gbx = fma(cq, Vqx, fma(k3, Vdx, rad * bx));
+    r.gby = fma(cq, Vqy, fma(k3, Vdy, rad * by));
+    r.gbz = fma(cq, Vqz, fma(k3, Vdz, rad * bz));
+    r.mx = dx;
+    r.my = dy;
+    r.mz = dz;
+    r.Et = E;
+    r.sqt = sq;
+    r.Dt = D;
+    r.rD = rD;
+    r.rs = rcp_newton(sq);
+    r.bx = bx;
+    r.by = by;
+    r.bz = bz;
+}
+
+__device__ __forceinline__ void cell_f64(const double* h, const double* muf, const CellG<double>& r,
+                                         const AdjConst<double>& c, double& tacc, double& aS, double& fbx,
+                                         double& fby, double& fbz) {
+    const double dS = sum19(h);
+    double sf[9], df[9];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        sf[p] = muf[2 * p + 1] + muf[2 * p + 2];
+        df[p] = muf[2 * p + 1] - muf[2 * p + 2];
+    }
+    const double F1 = wsum9(sf);  // sums times 36
+    double Vx, Vy, Vz;
+    wvec9(df, Vx, Vy, Vz);
+    const double Fdq = fma(Vx, r.bx, fma(Vy, r.by, Vz * r.bz));
+    const double fa = c.c3_36 * dS;  // (3 S / c_l) / 36
+    // f^eq_{+-p} = w_p (S +- 3 S q_p / c_l)
+    tacc = dot19(muf, h) - fma(kW0 * muf[0], dS, fma(dS * (1.0 / 36.0), F1, fa * Fdq));
+    aS = fma(F1, 1.0 / 36.0, fma(c.c3_36, Fdq, kW0 * muf[0]));
+    fbx = fa * Vx;
+    fby = fa * Vy;
+    fbz = fa * Vz;
+}
+
+// recovery_adjoint with 1/D and 1/s given and d = M / c_l
+__device__ __forceinline__ void recovery_adjoint64(double a_eps, double abx, double aby, double abz,
+                                                   const CellG<double>& r, const AdjConst<double>& c, double& vE,
+                                                   double& vx, double& vy, double& vz) {
+    const double abD = fma(abx, r.bx, fma(aby, r.by, abz * r.bz)) * r.rD;
+    const double depsdE = fma(4.0 * r.Et, r.rs, -1.0);
+    vE = fma(a_eps, depsdE, -abD * (3.0 + depsdE));
+    const double cc = (c.three_cl * r.rs) * (abD - a_eps);  // 3 (ab.beta / D - a_eps) / s, times c_l
+    const double rD3 = 3.0 * r.rD;
+    vx = fma(cc, r.mx, abx * rD3);
+    vy = fma(cc, r.my, aby * rD3);
+    vz = fma(cc, r.mz, abz * rD3);
+}
+
+template <typename PUT>
+__device__ __forceinline__ void scatter_cell64(const double* muf, const double* mug, double aS, double vE, double vx,
+                                               double vy, double vz, const AdjConst<double>& c, PUT put) {
+    const double nuS = c.om * aS, nuE = c.om * vE;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) put(i, i, fma(c.omw, muf[i], nuS));
+    put(19, 0, fma(c.omw, mug[0], nuE));
+    const double ux = c.om_cl * vx, uy = c.om_cl * vy, uz = c.om_cl * vz;
+    const double t[9] = {ux, uy, uz, ux + uy, ux - uy, ux + uz, ux - uz, uy + uz, uy - uz};
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        put(20 + 2 * p, 2 * p + 1, fma(c.omw, mug[2 * p + 1], nuE) + t[p]);
+        put(21 + 2 * p, 2 * p + 2, fma(c.omw, mug[2 * p + 2], nuE) - t[p]);
+    }
+}
+
 // A ghost plane cell (non-periodic x): nobody reads its populations that do
 // not point into the lattice; the others are written by the scatter of x +- 1.
 // At the inflow plane (held at eq(n_in, eps_in, beta_in)) its adjoint adds
@@ -574,7 +756,10 @@ __global__ void __launch_bounds__(128, MINB)
         T mug[19];
         load_mu(mug, 19);
         CellG<T> r;
-        cell_g(h, mug, c, r);
+        if constexpr (sizeof(T) == 8)
+            cell_g64(h, mug, c, r);
+        else
+            cell_g(h, mug, c, r);
         // ---- f phase
 #pragma unroll
         for (int i = 0; i < 19; ++i) h[i] = A[RLB_CHK(i * S + idx + o.src(i), 38ll * S)];
@@ -586,17 +771,27 @@ __global__ void __launch_bounds__(128, MINB)
         T muf[19];
         load_mu(muf, 0);
         T tf, aS, fbx, fby, fbz;
-        cell_f(h, muf, r, c, tf, aS, fbx, fby, fbz);
+        if constexpr (sizeof(T) == 8)
+            cell_f64(h, muf, r, c, tf, aS, fbx, fby, fbz);
+        else
+            cell_f(h, muf, r, c, tf, aS, fbx, fby, fbz);
         tau_acc += (r.tacc + tf) * c.inv_tau2_t;
         T vE, vx, vy, vz;
-        recovery_adjoint<T>(r.ae, fbx + r.gbx, fby + r.gby, fbz + r.gbz, r.Et, r.sqt, r.Dt, r.bx, r.by, r.bz, r.mx,
-                            r.my, r.mz, vE, vx, vy, vz);
-        scatter_cell(muf, mug, aS, vE, vx, vy, vz, c, [&](int q, int i, T v) {
+        if constexpr (sizeof(T) == 8)
+            recovery_adjoint64(r.ae, fbx + r.gbx, fby + r.gby, fbz + r.gbz, r, c, vE, vx, vy, vz);
+        else
+            recovery_adjoint<T>(r.ae, fbx + r.gbx, fby + r.gby, fbz + r.gbz, r.Et, r.sqt, r.Dt, r.bx, r.by, r.bz,
+                                r.mx, r.my, r.mz, vE, vx, vy, vz);
+        auto put = [&](int q, int i, T v) {
             if ((bounced >> i) & 1u)
                 Lout[RLB_CHK((q - i + opp(i)) * S + idx, 38ll * S)] = v;
             else
                 Lout[RLB_CHK(q * S + idx + o.src(i), 38ll * S)] = v;
-        });
+        };
+        if constexpr (sizeof(T) == 8)
+            scatter_cell64(muf, mug, aS, vE, vx, vy, vz, c, put);
+        else
+            scatter_cell(muf, mug, aS, vE, vx, vy, vz, c, put);
         zero_to_ghost<T, XBC>(x, g.nx, idx, S, Lout);
     }
     warp_partials<T>((double)tau_acc, bin0, bin1, bin2, has_b, red);
@@ -1203,10 +1398,11 @@ static int adjoint_step_t(const Geom& g, const Phys& ph, const T* A, const T* Li
         }
     }
     if constexpr (sizeof(T) == 8) {
+        // persistent (the instantiation the allocation-free step runs too)
         switch (g.xbc) {
-            case XBC_PERIODIC: warps = go(k_adjoint_step<T, XBC_PERIODIC, 2, false>, false, 2); break;
-            case XBC_INFLOW_OUTFLOW: warps = go(k_adjoint_step<T, XBC_INFLOW_OUTFLOW, 2, false>, false, 2); break;
-            default: warps = go(k_adjoint_step<T, XBC_OUTFLOW_BOTH, 2, false>, false, 2); break;
+            case XBC_PERIODIC: warps = go(k_adjoint_step<T, XBC_PERIODIC, 2, true>, true, 2); break;
+            case XBC_INFLOW_OUTFLOW: warps = go(k_adjoint_step<T, XBC_INFLOW_OUTFLOW, 2, true>, true, 2); break;
+            default: warps = go(k_adjoint_step<T, XBC_OUTFLOW_BOTH, 2, true>, true, 2); break;
         }
     } else if (g.adj_pipe) {
         switch (g.xbc) {

@@ -118,6 +118,39 @@ def test_fp32_adjoint_kernels(case, mode, monkeypatch):
     sim.close()
 
 
+@pytest.mark.parametrize("scale", [1e-30, 1e30])
+@pytest.mark.parametrize("case", [CASES[1], CASES[2]], ids=["solid", "inflow"])
+def test_fp64_adjoint_scale_invariance(case, scale):
+    """The step is homogeneous of degree one in (f, g) (the equilibria of
+    Eqs. equil1s/equil2as/equil2bs are, through the closed-form recovery),
+    so its Jacobian is unchanged when the state is scaled: one FP64 adjoint
+    step at the state times 1e-30 or 1e+30 gives the same lambda_t and
+    dL/dbeta_in (a table of the inflow parameters), and dL/dtau =
+    sum mu (h - eq) / tau^2 times the scale.  Checks that the binary64
+    recovery's seeded reciprocals and square root work at any exponent."""
+    w, p, sim, st, gstate, rng = _setup(case, "fp64", 21)
+    lam_in = rng.normal(size=st.shape)
+    li = sim.cells_to_state(torch.from_numpy(lam_in).cuda())
+    scaled = torch.where(torch.isnan(gstate), gstate, gstate * scale)  # keeps the solid markers' bits
+    outs = []
+    for state in (gstate, scaled):
+        lo = torch.full_like(li, float("nan"))
+        acc = torch.zeros(4, dtype=torch.float64, device="cuda")
+        sim.adjoint_step(state, li, lo, acc[0:1], acc[1:4])
+        outs.append((lo, acc))
+    sim.sync()
+    (lo_a, acc_a), (lo_b, acc_b) = outs
+    a = sim.state_to_cells(lo_a).cpu().numpy()
+    b = sim.state_to_cells(lo_b).cpu().numpy()
+    assert not np.isnan(b).any()
+    assert _rel(b, a) <= 1e-12
+    ta, tb = float(acc_a[0]), float(acc_b[0])
+    assert abs(tb / scale - ta) <= 1e-12 * abs(ta)
+    assert np.max(np.abs(acc_b[1:].cpu().numpy() - acc_a[1:].cpu().numpy())) <= 1e-12 * max(
+        float(acc_a[1:].abs().max()), 1e-300)
+    sim.close()
+
+
 @pytest.mark.parametrize("case", [CASES[2], CASES[4]], ids=["inflow", "ragged"])
 def test_fp32_adjoint_unaligned_lambda(case):
     """A lambda_{t+1} buffer that is not 16-byte aligned (a view 4 bytes into
