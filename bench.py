@@ -815,16 +815,21 @@ def run_profile(args):
     """Short runs of the benchmark workload for ncu captures: --profile step
     runs warm-up + --steps forward steps; --profile adjoint runs --steps
     (forward recompute + adjoint) steps; --profile box / adjoint_box run
-    forward / adjoint steps on the periodic random box of side --box."""
+    forward / adjoint steps on the periodic random box of side --box;
+    --profile tube runs FP64 steps of the 1600-cell shock tube."""
     import torch
 
     import workloads as W
     from paper_0912_2913_gb300 import RLB
 
     on_box = args.profile in ("box", "adjoint_box")
-    w = W.random_box(L=args.box, steps=args.steps) if on_box else W.sphere_3d(steps=args.steps)
+    if args.profile == "tube":
+        w = W.shock_tube_1d(steps=args.steps)
+        args.precision = "fp64"
+    else:
+        w = W.random_box(L=args.box, steps=args.steps) if on_box else W.sphere_3d(steps=args.steps)
     sim = RLB.from_workload(w, args.precision, device="cuda:0").init_fields(w.n, w.eps, w.beta, w.solid)
-    if args.profile in ("step", "box"):
+    if args.profile in ("step", "box", "tube"):
         sim.step(args.steps)
     else:
         sim.step(5)
@@ -851,7 +856,7 @@ def main(argv=None):
     ap.add_argument("--grad-steps", type=int, default=2000,
                     help="steps of the whole-gradient leg (rlb_run forward + backward); 0 skips it")
     ap.add_argument("--workload", choices=["box512", "sphere"], default="box512")
-    ap.add_argument("--profile", choices=["step", "adjoint", "box", "adjoint_box"], default=None,
+    ap.add_argument("--profile", choices=["step", "adjoint", "box", "adjoint_box", "tube"], default=None,
                     help="short run of one kernel family for ncu captures (no JSON bench line)")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--box", type=int, default=256)

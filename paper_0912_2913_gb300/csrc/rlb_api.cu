@@ -242,6 +242,8 @@ rlb_status rlb_create(const rlb_params* p, void* stream, void* workspace, size_t
         // the all-FP64 step, which stays the default)
         const char* fa = getenv("RLB_F64_ARITH");
         g.f64df = (fa && fa[0] == 'd' && fa[1] == 'f') ? 1 : 0;
+        const char* fs = getenv("RLB_F64_SPLIT");
+        g.f64split = fs ? (fs[0] == '1' ? 1 : 0) : -1;
     }
     Phys& ph = c->ph;
     ph.tau = p->tau;

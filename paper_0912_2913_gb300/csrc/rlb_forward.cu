@@ -31,6 +31,34 @@ void set_last_launch_count(int n) { g_last_launches = n; }
 // ---------------------------------------------------------------------------
 // FP64 step.
 // ---------------------------------------------------------------------------
+
+// Moments S_f, E and d = M / c_l of the FP64 step, summed as a fixed tree
+// over eight partials: partial j holds pair j, and for j < 2 also unit
+// j + 8 (pair 8 for j = 0, the rest population for j = 1).  They are combined
+// as ((P0 + P4) + (P2 + P6)) + ((P1 + P5) + (P3 + P7)), the order in which an
+// xor butterfly over eight lanes (offsets 4, 2, 1) adds them on every lane,
+// so k_step_f64_split, which spreads the units of a cell over eight lanes,
+// forms the same sums; the partials of d that are identically zero are left
+// out here (adding an exact zero leaves any value but -0 unchanged).
+__device__ __forceinline__ void moments_tree8(const double* f, const double* g, double& sf, double& e, double& dx,
+                                              double& dy, double& dz) {
+    double sp[9], ep[9], d[9];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        sp[p] = f[2 * p + 1] + f[2 * p + 2];
+        ep[p] = g[2 * p + 1] + g[2 * p + 2];
+        d[p] = g[2 * p + 1] - g[2 * p + 2];
+    }
+    const double s0 = sp[0] + sp[8], s1 = sp[1] + f[0];
+    const double e0 = ep[0] + ep[8], e1 = ep[1] + g[0];
+    sf = ((s0 + sp[4]) + (sp[2] + sp[6])) + ((s1 + sp[5]) + (sp[3] + sp[7]));
+    e = ((e0 + ep[4]) + (ep[2] + ep[6])) + ((e1 + ep[5]) + (ep[3] + ep[7]));
+    // x: pairs 0, 3, 4, 5, 6; y: 1, 3, -4, 7, 8; z: 2, 5, -6, 7, -8
+    dx = ((d[0] + d[4]) + d[6]) + (d[5] + d[3]);
+    dy = (d[8] - d[4]) + (d[1] + (d[3] + d[7]));
+    dz = (-d[8] + (d[2] - d[6])) + (d[5] + d[7]);
+}
+
 template <int XBC, bool SOLID>
 __global__ void __launch_bounds__(128) k_step_f64(const double* __restrict__ A, double* __restrict__ B, Geom g,
                                                   Phys ph, Counters cnt, int count, long long step_index) {
@@ -75,7 +103,7 @@ __global__ void __launch_bounds__(128) k_step_f64(const double* __restrict__ A, 
     }
     // d = M / c_l (the pair differences summed along each axis)
     double sf, E, dx, dy, dz;
-    moments_pairs(f, gg, sf, E, dx, dy, dz);
+    moments_tree8(f, gg, sf, E, dx, dy, dz);
     // Recovery with eps = 3P: eps = -E + sqrt(4E^2 - 3M^2), beta = 3M/(3E + eps).
     // Square root and reciprocals from binary32 seeds (converted on the integer
     // pipe, valid for any exponent of the argument) with two FP64 Newton
@@ -151,6 +179,191 @@ __global__ void __launch_bounds__(128) k_step_f64(const double* __restrict__ A, 
         }
     }
     if (count) count_flags(cnt, unphys, nonpos, (unsigned long long)step_index * (unsigned long long)g.N + idx);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 step for small lattices (the 1600-cell shock tube): eight lanes per
+// cell.  The FP64 pipe issues one warp instruction about every 76 cycles per
+// scheduler on this GPU (1.68 FMA per SM per clock), whatever the number of
+// active lanes, so a cell's ~200 FP64 instructions on one thread take some
+// 15,000 cycles however few cells share a scheduler.  Here lane j of a cell's
+// group pulls and relaxes pair j (and pair 8 for j = 0, the rest population
+// for j = 1); the moments are the lanes' partials summed by an xor butterfly
+// (the tree of moments_tree8), the recovery is repeated on every lane, and a
+// warp issues about half the FP64 instructions.  The arithmetic is that of
+// k_step_f64 term for term, so the two give the same values.
+// ---------------------------------------------------------------------------
+template <int XBC, bool SOLID>
+__global__ void __launch_bounds__(128) k_step_f64_split(const double* __restrict__ A, double* __restrict__ B, Geom g,
+                                                        Phys ph, Counters cnt, int count, long long step_index) {
+    const unsigned full = 0xffffffffu;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = threadIdx.x & 7;  // lane of the cell's group
+    const long long cell = t >> 3;
+    const bool live = cell < g.N;
+    const int idx = live ? (int)cell : 0;
+    int x, y, z;
+    cell_coords(g, idx, x, y, z);
+    const bool halo = g.zhalo && (z == 0 || z == g.nz - 1);  // filled by the exchange
+    const bool ghost = XBC != XBC_PERIODIC && (x == 0 || x == g.nx - 1);
+    const bool work = live && !halo && !ghost;  // a collided cell
+    const long long S = g.S;
+    const PullOffsets o(g, x, y, z);
+    // this lane's populations: pair j (a: +, b: -); lane 0 also pair 8
+    // (c: +, d: -), lane 1 the rest population (c)
+    const int ia = 2 * j + 1, ib = 2 * j + 2;
+    auto pull = [&](int i, double& fv, double& gv) {
+        const int src = idx + o.src(i);
+        fv = __ldg(RLB_CHK_PTR(A, i * S + src, 38ll * S));
+        gv = __ldg(RLB_CHK_PTR(A, (19 + i) * S + src, 38ll * S));
+        if (SOLID && is_solid(fv)) {  // link bounce-back
+            fv = __ldg(RLB_CHK_PTR(A, opp(i) * S + idx, 38ll * S));
+            gv = __ldg(RLB_CHK_PTR(A, (19 + opp(i)) * S + idx, 38ll * S));
+        }
+    };
+    double fa = 0.0, fb = 0.0, ga = 0.0, gb = 0.0, fc = 0.0, fd = 0.0, gc = 0.0, gd = 0.0;
+    bool own_solid = false;
+    if (work) {
+        pull(ia, fa, ga);
+        pull(ib, fb, gb);
+        if (j == 0) {
+            pull(17, fc, gc);
+            pull(18, fd, gd);
+        } else if (j == 1) {
+            fc = __ldg(RLB_CHK_PTR(A, idx, 38ll * S));
+            gc = __ldg(RLB_CHK_PTR(A, 19 * S + idx, 38ll * S));
+            own_solid = SOLID && is_solid(fc);
+        }
+    }
+    const bool solid = __shfl_sync(full, own_solid, (threadIdx.x & 24) + 1);  // lane 1 holds f_0
+    // partials of the moments (the tree of moments_tree8)
+    double ps = fa + fb, pe = ga + gb;
+    const double dj = ga - gb;
+    if (j == 0) {
+        ps = ps + (fc + fd);
+        pe = pe + (gc + gd);
+    } else if (j == 1) {
+        ps = ps + fc;
+        pe = pe + gc;
+    }
+    const double d8 = gc - gd;  // pair 8 on lane 0
+    const int ex = pair_ex(j), ey = pair_ey(j), ez = pair_ez(j);
+    double px = ex ? dj : 0.0;
+    double py = j == 0 ? d8 : (ey > 0 ? dj : (ey < 0 ? -dj : 0.0));
+    double pz = j == 0 ? -d8 : (ez > 0 ? dj : (ez < 0 ? -dj : 0.0));
+#pragma unroll
+    for (int off = 4; off > 0; off >>= 1) {
+        ps += __shfl_xor_sync(full, ps, off);
+        pe += __shfl_xor_sync(full, pe, off);
+        px += __shfl_xor_sync(full, px, off);
+        py += __shfl_xor_sync(full, py, off);
+        pz += __shfl_xor_sync(full, pz, off);
+    }
+    const double sf = ps, E = pe, dx = px, dy = py, dz = pz;
+    // recovery: as in k_step_f64
+    const double m2 = fma(dx, dx, fma(dy, dy, dz * dz));
+    const double disc = fma(4.0 * E, E, ph.m3cl2 * m2);
+    double ys, hs;
+    rsqrt_seed(disc, ys, hs);
+    double sq = disc * ys;
+    sq = fma(fma(-sq, sq, disc), hs, sq);
+    sq = fma(fma(-sq, sq, disc), hs, sq);
+    const double eps = sq - E;
+    const double D = fma(3.0, E, eps);
+    double rD = rcp_seed(D);
+    rD = fma(rD, fma(-D, rD, 1.0), rD);
+    rD = fma(rD, fma(-D, rD, 1.0), rD);
+    const double r3 = ph.three_cl * rD;
+    const double bx = dx * r3, by = dy * r3, bz = dz * r3;
+    const double b2 = fma(bx, bx, fma(by, by, bz * bz));
+    const double omb2 = 1.0 - b2;
+    double gam2 = rcp_seed(omb2);
+    gam2 = fma(gam2, fma(-omb2, gam2, 1.0), gam2);
+    gam2 = fma(gam2, fma(-omb2, gam2, 1.0), gam2);
+    const bool unphys = !(pos_finite(sf) && pos_finite(E) && nonneg_finite(disc) && pos_finite(eps) && below_one(b2));
+    const bool nonpos = nonpositive_eq(d2f(bx), d2f(by), d2f(bz), (float)ph.c_l);
+    // equilibria and relaxation of this lane's populations: as in k_step_f64
+    const double omw = 1.0 - ph.omega;
+    const double q[9] = {bx, by, bz, bx + by, bx - by, bx + bz, bx - bz, by + bz, by - bz};
+    const double eg = eps * gam2;
+    const double egb2 = eg * b2;
+    const double tt = fma(-2.0, egb2, eps);
+    const double k1w[2] = {tt * ph.c_k1[0], tt * ph.c_k1[1]};
+    const double k2w[2] = {eg * ph.c_k2[0], eg * ph.c_k2[1]};
+    const double k3w[2] = {eg * ph.c_k3[0], eg * ph.c_k3[1]};
+    const double fsw[2] = {sf * ph.c_fs[0], sf * ph.c_fs[1]};
+    const double faw[2] = {sf * ph.c_fa[0], sf * ph.c_fa[1]};
+    double qj = q[0];
+#pragma unroll
+    for (int p = 1; p < 8; ++p) qj = j == p ? q[p] : qj;
+    const int cl = j < 3 ? 0 : 1;
+    const double fsc = cl ? fsw[1] : fsw[0], fac = cl ? faw[1] : faw[0];
+    const double k1c = cl ? k1w[1] : k1w[0], k2c = cl ? k2w[1] : k2w[0], k3c = cl ? k3w[1] : k3w[0];
+    const double ofa = fma(omw, fa, fma(fac, qj, fsc));
+    const double ofb = fma(omw, fb, fma(-fac, qj, fsc));
+    const double gsym = fma(k2c, qj * qj, k1c);
+    const double oga = fma(omw, ga, fma(k3c, qj, gsym));
+    const double ogb = fma(omw, gb, fma(-k3c, qj, gsym));
+    double ofc, ofd = 0.0, ogc, ogd = 0.0;
+    if (j == 0) {  // pair 8 (diagonal weight)
+        ofc = fma(omw, fc, fma(faw[1], q[8], fsw[1]));
+        ofd = fma(omw, fd, fma(-faw[1], q[8], fsw[1]));
+        const double gs8 = fma(k2w[1], q[8] * q[8], k1w[1]);
+        ogc = fma(omw, gc, fma(k3w[1], q[8], gs8));
+        ogd = fma(omw, gd, fma(-k3w[1], q[8], gs8));
+    } else {  // the rest population (lane 1)
+        ofc = fma(omw, fc, sf * ph.c_f0);
+        ogc = fma(omw, gc, fma(eg, ph.c_g0[0], fma(eps, ph.c_g0[1], egb2 * ph.c_g0[2])));
+    }
+    auto put = [&](int i, long long at, double fv, double gv) {
+        B[RLB_CHK(i * S + at, 38ll * S)] = fv;
+        B[RLB_CHK((19 + i) * S + at, 38ll * S)] = gv;
+    };
+    if (work) {
+        if (solid) {  // the cell itself is solid: keep the marker
+            const double m = solid_marker_d();
+            put(ia, idx, m, m);
+            put(ib, idx, m, m);
+            if (j == 0) {
+                put(17, idx, m, m);
+                put(18, idx, m, m);
+            } else if (j == 1) {
+                put(0, idx, m, m);
+            }
+        } else {
+            auto put_all = [&](long long at) {
+                put(ia, at, ofa, oga);
+                put(ib, at, ofb, ogb);
+                if (j == 0) {
+                    put(17, at, ofc, ogc);
+                    put(18, at, ofd, ogd);
+                } else if (j == 1) {
+                    put(0, at, ofc, ogc);
+                }
+            };
+            put_all(idx);
+            if (XBC != XBC_PERIODIC && x == g.nx - 2) put_all(idx + 1);  // outflow ghost x = nx-1 copies x = nx-2
+            if (XBC == XBC_OUTFLOW_BOTH && x == 1) put_all(idx - 1);      // outflow ghost x = 0 copies x = 1
+        }
+    } else if (XBC == XBC_INFLOW_OUTFLOW && live && !halo && x == 0) {
+        // the inflow plane keeps its fixed equilibrium (copied)
+        auto copy = [&](int i) {
+            B[RLB_CHK(i * S + idx, 38ll * S)] = __ldg(RLB_CHK_PTR(A, i * S + idx, 38ll * S));
+            B[RLB_CHK((19 + i) * S + idx, 38ll * S)] = __ldg(RLB_CHK_PTR(A, (19 + i) * S + idx, 38ll * S));
+        };
+        copy(ia);
+        copy(ib);
+        if (j == 0) {
+            copy(17);
+            copy(18);
+        } else if (j == 1) {
+            copy(0);
+        }
+    }
+    if (count) {
+        const bool mine = j == 0 && work && !solid;
+        count_flags(cnt, mine && unphys, mine && nonpos, (unsigned long long)step_index * (unsigned long long)g.N + idx);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -563,6 +776,13 @@ static void launch_step_t(int prec, const Geom& g, const Phys& ph, const void* A
         const int tb = step_block(g.N, 128);
         if (g.f64df) {
             launch_step_f64_df(g, ph, A, B, cnt, count, step_index, st, tb);
+            return;
+        }
+        // eight lanes per cell while the lanes fit one warp per scheduler
+        // (N <= 16 x SMs), unless RLB_F64_SPLIT says otherwise; same values
+        if (g.f64split == 1 || (g.f64split < 0 && g.N <= 16ll * sm_count())) {
+            k_step_f64_split<XBC, SOLID><<<blocks_for(8 * g.N, 128), 128, 0, st>>>(
+                (const double*)A, (double*)B, g, ph, cnt, count ? 1 : 0, step_index);
             return;
         }
         k_step_f64<XBC, SOLID><<<blocks_for(g.N, tb), tb, 0, st>>>((const double*)A, (double*)B, g, ph, cnt,

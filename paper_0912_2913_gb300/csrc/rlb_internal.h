@@ -42,6 +42,7 @@ struct Geom {
     int adj_coop;   // staged FP32 adjoint: 1 lambda copied by the whole block (default), 0 per thread
     int zhalo;      // 1: planes z = 0 and z = nz-1 are halo copies, not updated by a step
     int f64df;      // 1: the FP64 step computes in compensated binary32 pairs (ablation)
+    int f64split;   // FP64 step with eight lanes per cell: -1 small lattices, 0 never, 1 always (tests)
 };
 
 // Physical parameters, with the derived constants the kernels use.

@@ -445,3 +445,31 @@ def test_fields_scaled_far_outside_binary32_squares(scale, prec):
     n0, e0, b0 = base
     tol = 1e-11 if prec == "fp64" else TOL[prec]
     assert max(rel_errors((n / scale, e / scale, b), (n0, e0, b0))) <= tol
+
+
+@pytest.mark.parametrize("name,make", [
+    ("shock_tube", lambda: W.shock_tube_1d()),
+    ("inflow_solid", lambda: tiny_workload(37, 9, 5, 1, seed=41, solid_cells=((12, 4, 2), (13, 4, 2), (12, 5, 2)))),
+    ("outflow_both_nx3", lambda: tiny_workload(3, 4, 5, 2, seed=42)),
+    ("periodic_ragged", lambda: tiny_workload(13, 7, 11, 0, seed=43)),
+    ("sphere_60", lambda: W.sphere_3d(nx=60, ny=30, nz=30)),
+], ids=lambda v: v if isinstance(v, str) else "")
+def test_fp64_split_step_equals_the_one_thread_step(name, make, monkeypatch):
+    """The FP64 step with eight lanes per cell (k_step_f64_split, the small
+    lattices' kernel) does the one-thread kernel's arithmetic term for term
+    (the moments summed in the same tree), so both give the same values and
+    statistics; RLB_F64_SPLIT forces either kernel on any lattice."""
+    w = make()
+    runs = []
+    for force in ("0", "1"):
+        monkeypatch.setenv("RLB_F64_SPLIT", force)
+        (n, e, b), sim = gpu_run(w, 40, "fp64")
+        state = sim.state()[:, :sim.N].clone()
+        runs.append(((n, e, b), state, sim.stats()))
+        sim.close()
+    (m0, s0, st0), (m1, s1, st1) = runs
+    for a, c in zip(m0, m1):
+        assert np.array_equal(a, c, equal_nan=True)
+    assert torch.equal(s0.isnan(), s1.isnan())
+    assert torch.equal(torch.nan_to_num(s0), torch.nan_to_num(s1))
+    assert st0 == st1
