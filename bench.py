@@ -44,11 +44,12 @@ if ROOT not in sys.path:
 METRIC = "MLUPS and % of HBM roofline, FP32 vs FP64, forward and adjoint step, 1 GB300"
 FALLBACK_HBM_GBS = 6800.0
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (vector and tensor), nominal
-# FP64 pipe instructions of one update of the all-FP64 step (57 moment
-# additions, ~28 recovery operations, ~125 equilibrium + BGK operations) and
-# the FP64 instruction rate derived from the nominal FP64 peak (1.25 TFLOP/s =
-# 625 G fused multiply-adds per second, one FP64 pipe instruction each).
-FP64_OPS_PER_UPDATE = 210
+# FP64 pipe instructions of one update of the all-FP64 step, counted by ncu
+# (smsp__inst_executed_pipe_fp64 per 32-cell warp of k_step_f64: 57 moment
+# additions, the recovery, the equilibria and BGK), and the FP64 instruction
+# rate derived from the nominal FP64 peak (1.25 TFLOP/s = 625 G fused
+# multiply-adds per second, one FP64 pipe instruction each).
+FP64_OPS_PER_UPDATE = 203
 FP64_PEAK_GOPS = FP64_NOMINAL_TFLOPS * 1e3 / 2
 
 # Algorithmic bytes per lattice update (every population read once and written once).
