@@ -212,12 +212,11 @@ RLB_API rlb_status rlb_adjoint_step(rlb_ctx* ctx, const void* state_t, const voi
  * memory at the point of the call -- code running under a caching allocator
  * or memory pool that owns all device memory, or a real-time loop that must
  * not synchronise (cudaMalloc/cudaFree can synchronise the device).
- * Same arguments, results and errors as rlb_adjoint_step.  It always runs the
- * persistent one-cell-per-thread register kernel of the adjoint (a grid of
- * SMs x 2 blocks for FP64, x 4 for FP32, capped at N/128 blocks), not the
- * staged FP32 kernel that rlb_adjoint_step uses by default, so its speed
- * differs; its results agree with rlb_adjoint_step's to rounding (the sums
- * are grouped by another grid).  The per-warp partial sums live in one static
+ * Same arguments, results and errors as rlb_adjoint_step, and the same
+ * kernels: FP64 the persistent register kernel (SMs x 2 blocks), FP32 the
+ * persistent shared-memory staged kernel (SMs x 3 blocks of 128; with
+ * RLB_ADJ_PIPE=0 or 1 the persistent register kernel, SMs x 4 blocks), grids
+ * capped at N/128 blocks.  The per-warp partial sums live in one static
  * device array of 32768 doubles (256 KiB) per device: a launch that would
  * need more (16 doubles per block) returns RLB_ERR_ARG and enqueues nothing;
  * every launch writes all the slots it reads, so nothing needs to start at

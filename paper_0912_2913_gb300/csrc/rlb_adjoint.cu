@@ -1525,6 +1525,19 @@ cudaError_t scratch_for_device(int dev, double** ptr, int* nsm) {
             e = cudaFuncGetAttributes(&attr, k);
             if (e != cudaSuccess) return e;
         }
+        // the FP32 staged kernels (block-copy and per-thread forms): loaded,
+        // and their shared memory opted in
+        const void* staged[] = {
+            (const void*)k_adjoint_step_coop<XBC_PERIODIC>,   (const void*)k_adjoint_step_coop<XBC_INFLOW_OUTFLOW>,
+            (const void*)k_adjoint_step_coop<XBC_OUTFLOW_BOTH>, (const void*)k_adjoint_step_staged<XBC_PERIODIC>,
+            (const void*)k_adjoint_step_staged<XBC_INFLOW_OUTFLOW>, (const void*)k_adjoint_step_staged<XBC_OUTFLOW_BOTH>,
+        };
+        for (const void* k : staged) {
+            cudaFuncAttributes attr;
+            e = cudaFuncGetAttributes(&attr, k);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageSmemBytes);
+            if (e != cudaSuccess) return e;
+        }
         s.nsm = n;
         s.ctx = ctx;
         s.ptr = p;
@@ -1567,8 +1580,21 @@ cudaError_t launch_adjoint_step_noalloc(int prec, const Geom& g, const Phys& ph,
     int nsm = 0;
     e = scratch_for_device(dev, &red, &nsm);
     if (e != cudaSuccess) return e;
-    const int minb = prec == 0 ? 2 : 4;
     const int nb = adj_blocks(g.N);
+    if (prec != 0 && g.adj_pipe == 2) {
+        // FP32 with the default kernel choice: the staged kernel that
+        // rlb_adjoint_step runs (persistent, SMs x 3 blocks of 128)
+        const int grid3 = nsm * 3 < nb ? nsm * 3 : nb;
+        const long long need = 16ll * grid3;
+        if (need_doubles) *need_doubles = need;
+        if (need > kAdjScratchDoubles) return cudaErrorInvalidValue;
+        set_last_launch_count(2);
+        const int warps = adjoint_step_t<float>(g, ph, (const float*)A, (const float*)lam_in, (float*)lam_out, red, nb,
+                                                inflow_d, st);
+        k_finalize<<<1, 1024, 0, st>>>(red, warps, dtau, dbeta_in);
+        return cudaGetLastError();
+    }
+    const int minb = prec == 0 ? 2 : 4;
     const int grid = nsm * minb < nb ? nsm * minb : nb;
     const long long need = 16ll * grid;  // 4 warps x 4 partial sums per block
     if (need_doubles) *need_doubles = need;

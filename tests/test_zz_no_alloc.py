@@ -1,6 +1,7 @@
 """rlb_adjoint_step_noalloc (the allocation-free adjoint step) against
 rlb_adjoint_step, through the C ABI: two calls in a row of each on the same
-inputs, lambda_t and both accumulated sums compared after every call.
+inputs, lambda_t and both accumulated sums compared after every call (the
+two entry points run the same kernels on the same grids, so bit for bit).
 
 Kept in its own file, collected last, so that it also runs after everything
 else has used the library in this process."""
@@ -98,6 +99,9 @@ def test_noalloc_adjoint_step_matches_adjoint_step(case, prec):
             assert _rel(acc_b[1:4], acc_a[1:4]) <= TOL[prec]
         else:
             assert acc_b[1:4].abs().max().item() == 0
+        ints = torch.int64 if prec == "fp64" else torch.int32
+        assert torch.equal(lb_out[:, :n].contiguous().view(ints), la_out[:, :n].contiguous().view(ints))
+        assert torch.equal(acc_b.view(torch.int64), acc_a.view(torch.int64))
         la_in, la_out = la_out, la_in
         lb_in, lb_out = lb_out, lb_in
     st = N.rlb_stats(sim.ctx)
