@@ -1109,16 +1109,8 @@ __global__ void __launch_bounds__(kStageThreads, 3)
         // ---- f phase, scatter
         if (!act) {
         } else if (ghost) {
-            // ghost_cell with lambda_t+1 from the ring
-            const int inward = (x == 0) ? 1 : -1;
-#pragma unroll
-            for (int i = 0; i < 19; ++i) {
-                if (vel_x(i) != inward) {
-                    *po(i, idx) = 0.0f;
-                    *po(19 + i, idx) = 0.0f;
-                }
-            }
-            // (the inflow plane's dL/dbeta_in terms: below, by the whole warp)
+            // ghost_cell: its zeros and the inflow plane's dL/dbeta_in terms
+            // are written below by the whole warp
         } else if (solid) {  // never updated: identity
 #pragma unroll
             for (int i = 0; i < 19; ++i) {
@@ -1157,7 +1149,32 @@ __global__ void __launch_bounds__(kStageThreads, 3)
                 else
                     *po(q, idx + o.src(i)) = v;
             });
-            zero_to_ghost<float, XBC>(x, g.nx, idx, S, Lout);
+        }
+        if constexpr (XBC != XBC_PERIODIC) {
+            // The zeros next to the ghost planes, spread over the warp (one
+            // lane storing 28 or 10 of them would hold its block at the next
+            // barrier): for each lane that is a ghost cell, lane q zeroes
+            // population q of it where nobody reads it (velocity not pointing
+            // inward); for each fluid cell at x = 1 or nx - 2, lane q zeroes
+            // population q of it where the ghost would have pulled it.
+            const int lane = tid & 31;
+            const int vq = lane < 19 ? vel_x(lane) : 0;
+            unsigned m = __ballot_sync(0xffffffffu, act && (ghost || (!solid && (x == 1 || x == g.nx - 2))));
+            while (m) {
+                const int src = __ffs(m) - 1;
+                m &= m - 1;
+                const int cx = __shfl_sync(0xffffffffu, x, src);
+                const int cidx = __shfl_sync(0xffffffffu, idx, src);
+                bool z;
+                if (cx == 0 || cx == g.nx - 1)
+                    z = vq != (cx == 0 ? 1 : -1);  // a ghost cell
+                else  // next to a ghost (both, when nx = 3)
+                    z = (cx == 1 && vq == -1) || (cx == g.nx - 2 && vq == 1);
+                if (lane < 19 && z) {
+                    Lout[RLB_CHK((long long)lane * S + cidx, 38ll * S)] = 0.0f;
+                    Lout[RLB_CHK((long long)(19 + lane) * S + cidx, 38ll * S)] = 0.0f;
+                }
+            }
         }
         if constexpr (XBC == XBC_INFLOW_OUTFLOW) {
             // dL/dbeta_in = lambda_t+1 . d eq_in / d beta_in at each fluid
