@@ -637,7 +637,8 @@ __device__ __forceinline__ void scatter_cell64(const double* muf, const double* 
 // not point into the lattice; the others are written by the scatter of x +- 1.
 // At the inflow plane (held at eq(n_in, eps_in, beta_in)) its adjoint adds
 // lambda_{t+1} . d eq_in / d beta_in (a per-context table).
-template <typename T, int XBC>
+// TERMS = false: only the zeros (the dL/dbeta_in terms taken elsewhere).
+template <typename T, int XBC, bool TERMS = true>
 __device__ __forceinline__ void ghost_cell(int x, int idx, long long S, const T* __restrict__ A,
                                            const T* __restrict__ Lin, T* __restrict__ Lout,
                                            const T* __restrict__ inflow_t, double& bin0, double& bin1,
@@ -650,7 +651,7 @@ __device__ __forceinline__ void ghost_cell(int x, int idx, long long S, const T*
             Lout[RLB_CHK((19 + i) * S + idx, 38ll * S)] = (T)0;
         }
     }
-    if (XBC == XBC_INFLOW_OUTFLOW && x == 0 && !is_solid(A[RLB_CHK(idx, 38ll * S)])) {
+    if (TERMS && XBC == XBC_INFLOW_OUTFLOW && x == 0 && !is_solid(A[RLB_CHK(idx, 38ll * S)])) {
         T a0 = 0, a1 = 0, a2 = 0;
 #pragma unroll 2
         for (int q = 0; q < 38; ++q) {
@@ -705,8 +706,34 @@ __global__ void __launch_bounds__(128, MINB)
         const int idx = (int)li;
         int x, y, z;
         cell_coords(g, idx, x, y, z);
+        if constexpr (sizeof(T) == 8 && XBC == XBC_INFLOW_OUTFLOW) {
+            // dL/dbeta_in at the fluid inflow ghosts of this warp, their 38
+            // products with the table spread over the active lanes (one lane
+            // issuing all 114 would take a full FP64 warp slot for each)
+            const unsigned act = __activemask();
+            unsigned m = __ballot_sync(act, x == 0 && !is_solid(A[RLB_CHK(idx, 38ll * S)]));
+            if (m) {
+                const int lane = threadIdx.x & 31;
+                const int rank = __popc(act & ((1u << lane) - 1u)), cnt = __popc(act);
+                while (m) {
+                    const int src = __ffs(m) - 1;
+                    m &= m - 1;
+                    const int gidx = __shfl_sync(act, idx, src);
+                    for (int q = rank; q < 38; q += cnt) {
+                        const T l = Lin[RLB_CHK((long long)q * S + gidx, 38ll * S)];
+                        bin0 = fma(l, inflow_t[3 * q + 0], bin0);
+                        bin1 = fma(l, inflow_t[3 * q + 1], bin1);
+                        bin2 = fma(l, inflow_t[3 * q + 2], bin2);
+                    }
+                    has_b = true;
+                }
+            }
+        }
         if ((XBC != XBC_PERIODIC) && (x == 0 || x == g.nx - 1)) {
-            ghost_cell<T, XBC>(x, idx, S, A, Lin, Lout, inflow_t, bin0, bin1, bin2, has_b);
+            if constexpr (sizeof(T) == 8 && XBC == XBC_INFLOW_OUTFLOW)
+                ghost_cell<T, XBC, false>(x, idx, S, A, Lin, Lout, inflow_t, bin0, bin1, bin2, has_b);
+            else
+                ghost_cell<T, XBC>(x, idx, S, A, Lin, Lout, inflow_t, bin0, bin1, bin2, has_b);
             continue;
         }
         if (is_solid(A[RLB_CHK(19 * S + idx, 38ll * S)])) {  // never updated: identity
