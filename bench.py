@@ -829,6 +829,8 @@ def run_profile(args):
         args.precision = "fp64"
     else:
         w = W.random_box(L=args.box, steps=args.steps) if on_box else W.sphere_3d(steps=args.steps)
+        if on_box:
+            w.c_l = args.c_l
     sim = RLB.from_workload(w, args.precision, device="cuda:0").init_fields(w.n, w.eps, w.beta, w.solid)
     if args.profile in ("step", "box", "tube"):
         sim.step(args.steps)
@@ -861,6 +863,7 @@ def main(argv=None):
                     help="short run of one kernel family for ncu captures (no JSON bench line)")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--box", type=int, default=256)
+    ap.add_argument("--c-l", dest="c_l", type=float, default=1.0, help="lattice speed of the --profile box runs")
     args = ap.parse_args(argv)
     if args.profile:
         run_profile(args)
