@@ -1381,6 +1381,50 @@ cudaError_t launch_adjoint_macro(int prec, const Geom& g, const Phys& ph, const 
     return cudaGetLastError();
 }
 
+namespace {
+// The calling thread's current context (the device's primary context under
+// the runtime API), through the driver entry point the runtime hands out, so
+// that the library needs no link against the driver library.
+CUcontext current_context() {
+    using Fn = CUresult (*)(CUcontext*);
+    static Fn fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<Fn>(f);
+        looked = true;
+    }
+    CUcontext c = nullptr;
+    if (fn) fn(&c);
+    return c;
+}
+
+// The dynamic shared memory opt-in of a staged kernel, once per context and
+// kernel (the attribute belongs to the kernel in a context: a new context
+// after a reset needs it again; setting it on every launch costs a host-side
+// call that held back the launch queue of short steps).
+std::mutex g_optin_mu;
+struct OptIn {
+    CUcontext ctx;
+    const void* kern;
+};
+OptIn g_optin[64];
+int g_optin_n = 0;
+
+cudaError_t smem_opt_in(const void* kern, int bytes) {
+    const CUcontext ctx = current_context();
+    std::lock_guard<std::mutex> lock(g_optin_mu);
+    for (int i = 0; i < g_optin_n; ++i)
+        if (g_optin[i].ctx == ctx && g_optin[i].kern == kern) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && g_optin_n < 64) g_optin[g_optin_n++] = {ctx, kern};
+    return e;
+}
+}  // namespace
+
 template <typename T>
 static int adjoint_step_t(const Geom& g, const Phys& ph, const T* A, const T* Li, T* Lo, double* red, int nb,
                           const double* inflow_d, cudaStream_t st) {
@@ -1413,15 +1457,7 @@ static int adjoint_step_t(const Geom& g, const Phys& ph, const T* A, const T* Li
                 tab.o[q] = (float*)Lo + (long long)q * g.S;
             }
             auto staged = [&](auto kern) {
-                // the shared-memory opt-in, once per device and kernel
-                static unsigned char attr[64][6];
-                const int which = g.xbc + 3 * coop;
-                int dev = 0;
-                cudaGetDevice(&dev);
-                if (dev >= 0 && dev < 64 && !attr[dev][which]) {
-                    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageSmemBytes);
-                    attr[dev][which] = 1;
-                }
+                smem_opt_in((const void*)kern, (int)kStageSmemBytes);  // a failure shows at the launch
                 const int grid = persistent_grid(3);
                 kern<<<grid, kStageThreads, kStageSmemBytes, st>>>(A, Li, Lo, g, ph, c, red, inflow_t, tab);
                 return grid * (kStageThreads / 32);
@@ -1516,26 +1552,6 @@ struct ScratchSetup {
 };
 ScratchSetup g_scratch[kMaxDevices];
 
-// The calling thread's current context (the device's primary context under
-// the runtime API), through the driver entry point the runtime hands out, so
-// that the library needs no link against the driver library.
-CUcontext current_context() {
-    using Fn = CUresult (*)(CUcontext*);
-    static Fn fn = nullptr;
-    static bool looked = false;
-    if (!looked) {
-        void* f = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<Fn>(f);
-        looked = true;
-    }
-    CUcontext c = nullptr;
-    if (fn) fn(&c);
-    return c;
-}
-
 // Set-up, with the device current: the device address of g_adj_scratch, the
 // SM count, and every kernel this entry point launches loaded onto the
 // device (cudaFuncGetAttributes loads a kernel that lazy module loading has
@@ -1579,7 +1595,7 @@ cudaError_t scratch_for_device(int dev, double** ptr, int* nsm) {
         for (const void* k : staged) {
             cudaFuncAttributes attr;
             e = cudaFuncGetAttributes(&attr, k);
-            if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageSmemBytes);
+            if (e == cudaSuccess) e = smem_opt_in(k, (int)kStageSmemBytes);
             if (e != cudaSuccess) return e;
         }
         s.nsm = n;

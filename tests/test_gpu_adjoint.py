@@ -182,6 +182,48 @@ def test_fp32_adjoint_unaligned_lambda(case):
     sim.close()
 
 
+_FRESH_FALLBACK = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, ".")
+from tests._helpers import tiny_workload
+from paper_0912_2913_gb300 import RLB
+w = tiny_workload(37, 9, 5, 1, seed=23, solid_cells=((12, 4, 2),))
+sim = RLB.from_workload(w, "fp32", device="cuda:0").init_fields(w.n, w.eps, w.beta, w.solid)
+sim.step(2)
+s = sim.state()
+li = torch.zeros_like(s)
+li[:, :sim.N] = torch.randn(38, sim.N, generator=torch.Generator().manual_seed(5)).cuda()
+buf = torch.empty(li.numel() + 1, dtype=li.dtype, device=li.device)
+odd = buf[1:].view(li.shape)
+odd.copy_(li)
+outs = []
+for lam in (li, odd):  # the block-copy kernel first, then the per-thread fallback
+    lo = torch.full_like(li, float("nan"))
+    acc = torch.zeros(4, dtype=torch.float64, device="cuda")
+    sim.adjoint_step(s, lam, lo, acc[0:1], acc[1:4])
+    outs.append(lo)
+sim.sync()
+n = sim.N
+assert torch.equal(outs[0][:, :n].view(torch.int32), outs[1][:, :n].view(torch.int32))
+print("ok")
+"""
+
+
+def test_fp32_adjoint_fallback_in_a_fresh_process():
+    """In a process where nothing else ran, the block-copy staged kernel and
+    then, for a lambda buffer that is not 16-byte aligned, the per-thread
+    staged kernel: each launch opts its own kernel into the shared memory it
+    needs, whatever ran before it."""
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _FRESH_FALLBACK], cwd=root, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout[-2000:] + r.stderr[-2000:]
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("case", CASES[:3], ids=IDS[:3])
 def test_adjoint_macro_and_fields_parity(case, prec):
