@@ -17,9 +17,12 @@
 // back to the one-cell-per-thread kernel.  Waits are bounded (rlb_tma.cuh):
 // a CTA that gives up sets Counters::pipe_err, waits (bounded) for its own
 // copies still in flight, and returns.
+#include <cuda.h>  // CUcontext type only; cuCtxGetCurrent is taken through the runtime
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdlib.h>
+
+#include <mutex>
 
 #include "rlb_collide.cuh"
 #include "rlb_device.cuh"
@@ -164,6 +167,50 @@ int env_int(const char* name, int dflt) {
     const char* v = getenv(name);
     return (v && *v) ? atoi(v) : dflt;
 }
+
+// The calling thread's current context, through the driver entry point the
+// runtime hands out (no link against the driver library).
+CUcontext current_context() {
+    using Fn = CUresult (*)(CUcontext*);
+    static Fn fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<Fn>(f);
+        looked = true;
+    }
+    CUcontext c = nullptr;
+    if (fn) fn(&c);
+    return c;
+}
+
+// The dynamic shared memory opt-in of a kernel, per context and kernel (the
+// attribute belongs to the kernel in a context), raised when a launch needs
+// more than was set.
+std::mutex g_optin_mu;
+struct OptIn {
+    CUcontext ctx;
+    const void* kern;
+    size_t bytes;
+};
+OptIn g_optin[32];
+int g_optin_n = 0;
+
+void smem_opt_in(const void* kern, size_t bytes) {
+    const CUcontext ctx = current_context();
+    std::lock_guard<std::mutex> lock(g_optin_mu);
+    int k = 0;
+    while (k < g_optin_n && !(g_optin[k].ctx == ctx && g_optin[k].kern == kern)) ++k;
+    if (k < g_optin_n && g_optin[k].bytes >= bytes) return;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) return;
+    if (k < g_optin_n)
+        g_optin[k].bytes = bytes;
+    else if (g_optin_n < 32)
+        g_optin[g_optin_n++] = {ctx, kern, bytes};
+}
 }  // namespace
 
 cudaError_t launch_step_f32_tma(const Geom& g, const Dev32& c, const float* A, float* B, Counters cnt, bool count,
@@ -202,12 +249,8 @@ cudaError_t launch_step_f32_tma(const Geom& g, const Dev32& c, const float* A, f
     const int ctas_per_sm = env_int("RLB_TMA_CTAS", 1);
     int grid = nsm * ctas_per_sm;
     if (grid > tc.ntiles) grid = tc.ntiles;
-    static size_t smem_set[6] = {0, 0, 0, 0, 0, 0};
-    auto run = [&](auto kern, int which) {
-        if (smem_set[which] < smem) {
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            smem_set[which] = smem;
-        }
+    auto run = [&](auto kern, int) {
+        smem_opt_in((const void*)kern, smem);  // a failure shows at the launch
         kern<<<grid, threads, smem, st>>>(A, B, g, c, cnt, count ? 1 : 0, step_index, tc);
     };
     if (minb == 3) {
